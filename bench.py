@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Joint-MM beta-NMF benchmark on one GB300 (replicas on N GPUs).
+
+Default workload: dense quadratic-loss NMF (beta = 2) shaped like a face-image
+collection, F = 361 (19 x 19 pixels), N = 2429 images, K = 49; synthetic data
+(paper_2106_15214_gb300.inputs.dense_quadratic_faces). One step is one outer
+JMM iteration (Algorithm 2, L = 1): the product at the iterate, both factor
+updates, the objective at the iterate and the normalisation. The metric is
+JMM iterations/s; beside it: the dominant kernel's roofline, the host-buffer
+end-to-end rate, the CPU oracle's rate, and the time to the paper's stopping
+tolerance of JMM against alternating MU (BMM) on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "joint-MM iters/s"
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "faces": dict(gen="dense_quadratic_faces", beta=2.0, desc="dense quadratic (beta=2) faces F=361 N=2429 K=49"),
+    "spectrogram": dict(gen="dense_is_spectrogram", beta=0.0, desc="dense Itakura-Saito (beta=0) F=513 N=20000 K=20"),
+    "kl_small": dict(gen="dense_kl_small", beta=1.0, desc="dense KL (beta=1) F=200 N=500 K=10"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="faces", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, help="fp32 | tf32 | bf16 | fp64")
+    ap.add_argument("--order", default="W")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-ttt-iters", type=int, default=1000)
+    return ap.parse_args()
+
+
+def problem(name):
+    from paper_2106_15214_gb300 import inputs
+    wl = WORKLOADS[name]
+    return getattr(inputs, wl["gen"])(), wl
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def time_oracle(p, beta, seconds, max_iters=None, warmup=1):
+    """Oracle JMM iterations (as written, no tuning) on the host cores."""
+    import oracle as O
+    W, H = p.W0.copy(), p.H0.copy()
+    for _ in range(warmup):
+        W, H = O.jmm_iteration(p.V, W, H, beta)
+        W, H = O.normalize(W, H)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        _ = O.D_beta(p.V, W @ H, beta)
+        W, H = O.jmm_iteration(p.V, W, H, beta)
+        W, H = O.normalize(W, H)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_iters and n >= max_iters):
+            return n, el
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(kernel, F, N, K, esize=4, S=1):
+    """Minimal DRAM bytes one launch of `kernel` must move:
+    V once, the factors it reads, the numerators/denominators or factors it writes."""
+    V = F * N * esize
+    fac = (F * K + K * N) * esize
+    table = {
+        "row_sweep": V + fac + 2 * F * K * esize,
+        "col_sweep": V + fac + 2 * F * K * esize + 2 * K * N * esize,
+        "tc_jmm_fused": V + fac + 2 * F * K * esize,
+        "tc_sweep_w": V + fac + 2 * F * K * esize,
+        "tc_sweep_h": V + fac + 2 * F * K * esize + K * N * esize,
+    }
+    return table.get(kernel)
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import oracle as O
+    p, wl = problem(args.workload)
+    beta = wl["beta"]
+    W, H = p.W0.copy(), p.H0.copy()
+    for _ in range(args.warmup):
+        W, H = O.jmm_iteration(p.V, W, H, beta)
+        W, H = O.normalize(W, H)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _ = O.D_beta(p.V, W @ H, beta)
+        W, H = O.jmm_iteration(p.V, W, H, beta)
+        W, H = O.normalize(W, H)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = args.steps / tot
+    F, N, K = p.shape
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "F": F, "N": N, "K": K, "beta": beta,
+                   "step": "one JMM outer iteration (L=1) with objective and normalisation"},
+        "cpu_baseline": {"value": val, "unit": "iters/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} full JMM iterations of the workload (numpy FP64 oracle)"},
+        "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timing_records(m):
+    import ctypes
+    lib = m._lib
+    recs, i = [], 0
+    while True:
+        name, n, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+        if lib.nmf_get_timing(m._ctx, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)) != 0:
+            break
+        recs.append((name.value.decode(), n.value, ms.value))
+        i += 1
+    name, n, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+    lib.nmf_get_timing(m._ctx, -1, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms))
+    return recs, n.value
+
+
+def time_to_tolerance(p, beta, precision, method, tol, max_iters, order="W"):
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    F, N, K = p.shape
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    m = NMF(F, N, K, beta, precision=precision, order=order)
+    V = torch.tensor(p.V, dtype=dt, device="cuda")
+    W = torch.tensor(p.W0, dtype=dt, device="cuda")
+    H = torch.tensor(p.H0, dtype=dt, device="cuda")
+    m.set_dense(V)
+    m.set_factors(W, H)
+    step = m.step_joint if method == "jmm" else m.step_alternating
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prev = step(1)
+    it = 1
+    cur = prev
+    while it < max_iters:
+        cur = step(1)          # objective at the iterate entering this iteration
+        it += 1
+        if (prev - cur) / cur <= tol:
+            break
+        prev = cur
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    # objective of the returned factors, re-evaluated in FP64 on the GPU
+    m64 = NMF(F, N, K, beta, precision="fp64")
+    V64, W64, H64 = V.double(), W.double(), H.double()
+    m64.set_dense(V64)
+    m64.set_factors(W64, H64)
+    return {"s": el, "iters": it, "D": m64.loss(), "stopped_by_tol": it < max_iters}
+
+
+def run_ours(args):
+    import torch
+    from paper_2106_15214_gb300 import binding
+    from paper_2106_15214_gb300.binding import NMF
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    binding.load()
+    p, wl = problem(args.workload)
+    beta = wl["beta"]
+    F, N, K = p.shape
+    precision = args.precision or "fp32"
+    esize = 8 if precision == "fp64" else 4
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    m = NMF(F, N, K, beta, precision=precision, order=args.order)
+    V = torch.tensor(p.V, dtype=dt, device="cuda")
+    W = torch.tensor(p.W0, dtype=dt, device="cuda")
+    H = torch.tensor(p.H0, dtype=dt, device="cuda")
+    m.set_dense(V)
+    m.set_factors(W, H)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        m.step_joint(1)
+    m._lib.nmf_reset_timing(m._ctx)
+    m._lib.nmf_set_timing(m._ctx, 1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    losses = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))                 # L2 flush between steps (not timed)
+            starts[i].record(stream)
+            losses.append(m.step_joint(1))
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = reduce_max(dev_s, world)
+    recs, launches = timing_records(m)
+    m._lib.nmf_set_timing(m._ctx, 0)
+    value = world * args.steps / dev_s_max
+    # dominant kernel of the step and its roofline
+    dom = max(recs, key=lambda r: r[2]) if recs else None
+    roof = None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if dom:
+        name, n, ms = dom
+        per_launch_s = ms / 1e3 / max(n, 1)
+        ab = algorithmic_bytes(name, F, N, K, esize)
+        peak = peaks.get("hbm_gbs", 6800.0)
+        if ab:
+            ach = ab / per_launch_s / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "algorithmic_bytes": ab,
+                    "avg_launch_us": per_launch_s * 1e6, "launches": n,
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                    "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
+    kernels = {r[0]: {"launches": r[1], "ms": round(r[2], 4)} for r in recs}
+    # end to end through the host-buffer C-ABI call
+    Vh = torch.tensor(p.V, dtype=dt).pin_memory()
+    Wh = torch.tensor(p.W0, dtype=dt).pin_memory()
+    Hh = torch.tensor(p.H0, dtype=dt).pin_memory()
+    me = NMF(F, N, K, beta, precision=precision, order=args.order)
+    for _ in range(3):
+        me.step_joint_host(Vh, Wh, Hh, 1)
+    torch.cuda.synchronize()
+    e2e_steps = max(10, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        me.step_joint_host(Vh, Wh, Hh, 1)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "iters/s",
+           "h2d_bytes_per_step": (F * N + F * K + K * N) * esize,
+           "d2h_bytes_per_step": (F * K + K * N) * esize + 8}
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[precision],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "F": F, "N": N, "K": K, "beta": beta, "precision": precision,
+                   "order": args.order, "step": "one JMM outer iteration (L=1) with objective and normalisation",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof, "gpu_launches": launches, "kernels": kernels,
+        "e2e": e2e, "wall_s": wall,
+        "step_ms_median": statistics.median(step_ms),
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            n_it, el = time_oracle(p, beta, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": n_it / el, "unit": "iters/s", "cores": cpu_threads(), "kind": "oracle",
+                                    "sample": f"{n_it} full JMM iterations of the workload ({el:.1f} s, numpy FP64)"}
+        if not args.no_ttt:
+            tol = 1e-5
+            line["time_to_tolerance"] = {
+                "tol": tol, "rule": "(D_prev - D)/D <= tol, max %d iterations" % args.max_ttt_iters,
+                "jmm": time_to_tolerance(p, beta, precision, "jmm", tol, args.max_ttt_iters, args.order),
+                "bmm_same_precision": time_to_tolerance(p, beta, "fp32" if precision != "fp64" else "fp64", "bmm", tol,
+                                                        args.max_ttt_iters, args.order),
+                "bmm_fp64": time_to_tolerance(p, beta, "fp64", "bmm", tol, args.max_ttt_iters, args.order),
+            }
+    clocks = clk.summary()
+    line["clocks"] = clocks
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

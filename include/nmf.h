@@ -1,0 +1,194 @@
+/*
+ * nmf.h -- C ABI of the GB300 (sm_103a) joint-MM beta-NMF library (libnmf.so).
+ *
+ * Problem (Sec. 2.1, eq. nmf / obj_fct / beta-div): given a nonnegative
+ * F x N matrix V, find nonnegative W (F x K) and H (K x N) minimising
+ * D_beta(V | WH) = sum_fn d_beta(v_fn | [WH]_fn).
+ *
+ * Two iterations are offered on the same data:
+ *   - nmf_step_joint:       joint majorisation-minimisation, Algorithm 2 with
+ *                           the updates of eq. jnt_update (chi_1, chi_2, gamma
+ *                           of eq. def_gamma); Vt = Wt Ht is formed once per
+ *                           outer iteration and both factors are rescaled
+ *                           from the iterate (Wt, Ht).
+ *   - nmf_step_alternating: classic block MM, Algorithm 1 with eq. alt_update;
+ *                           WH is recomputed before each factor's update.
+ *
+ * Layouts: every matrix is row-major. V is F x N with leading dimension ldv
+ * (elements, ldv >= N). W is F x K (leading dimension K). H is K x N
+ * (leading dimension N). Element type: double for NMF_FP64, float for every
+ * other precision.
+ *
+ * Ownership: V, W, H, gradient outputs and CSR arrays are caller-owned DEVICE
+ * buffers that must stay valid while a context uses them; the library only
+ * borrows them. W and H are updated in place. The context owns its scratch
+ * (tilde copies, partial sums, loss buffers, status word) and frees it in
+ * nmf_destroy.
+ *
+ * Streams: every call is ordered on the stream given to nmf_set_options
+ * (default: the legacy default stream). Calls that return a host value
+ * (a non-NULL loss_out, nmf_loss, nmf_get_status, nmf_kkt) synchronise that
+ * stream; the rest are asynchronous.
+ *
+ * Errors: every call returns an nmf_status; nothing aborts and no exception
+ * crosses the ABI. Invalid sizes, non-finite beta, wrong precision/buffer
+ * combinations -> NMF_EINVAL; allocation failure -> NMF_ENOMEM; a CUDA error
+ * -> NMF_ECUDA. A non-finite value produced by an update sets a device status
+ * word; the kernels of later iterations then do nothing, and the next
+ * synchronising call returns NMF_ENONFINITE after restoring W and H to the
+ * last finite iterate.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NMF_OK = 0,
+  NMF_EINVAL = 1,        /* invalid argument */
+  NMF_ENOMEM = 2,        /* device or host allocation failed */
+  NMF_ECUDA = 3,         /* a CUDA runtime call failed */
+  NMF_ENONFINITE = 4,    /* an update produced Inf/NaN; W, H restored */
+  NMF_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  NMF_EUNSUPPORTED = 6,  /* valid request this build does not implement */
+  NMF_ENOTREADY = 7      /* data or factors not set yet */
+} nmf_status;
+
+typedef enum {
+  NMF_FP64 = 0,  /* double storage and arithmetic (SIMT DFMA) */
+  NMF_FP32 = 1,  /* float storage and arithmetic (SIMT FFMA) */
+  NMF_TF32 = 2,  /* float storage; products on tensor cores (tcgen05 kind::tf32),
+                    FP32 accumulation, powers in FP32, loss accumulated in FP64 */
+  NMF_BF16 = 3   /* float storage; tensor-core operands rounded to bf16
+                    (tcgen05 kind::f16), FP32 accumulation */
+} nmf_precision;
+
+typedef enum {
+  NMF_W_FIRST = 0,    /* W then H: the order of Algorithm 2 as printed */
+  NMF_H_FIRST = 1,    /* H then W: the inverted order of Sec. 4.1.1 */
+  NMF_ORDER_AUTO = 2  /* library picks (W_FIRST when F >= N, else H_FIRST) */
+} nmf_order;
+
+typedef struct nmf_ctx nmf_ctx; /* opaque */
+
+/* Creates a context for one F x N problem of rank K with divergence beta
+ * (eq. beta-div; any finite beta). F, N, K >= 1, else NMF_EINVAL. Allocates
+ * scratch lazily on the first step. Default options: NMF_FP32, NMF_W_FIRST,
+ * normalisation on (Sec. 4.1.2), kappa = 0, deterministic reductions, legacy
+ * default stream, one sub-iteration (L = 1). */
+nmf_status nmf_create(int64_t F, int64_t N, int32_t K, double beta, nmf_ctx** out);
+
+/* Creates a context holding `count` independent problems of sizes F[i] x N[i]
+ * with ranks K[i] (Sec. 4.5 workload shape); all share beta. Data are given
+ * packed by nmf_batch_set_packed. Each problem is iterated exactly as a
+ * single-problem context would iterate it. */
+nmf_status nmf_batch_create(int32_t count, const int64_t* F, const int64_t* N,
+                            const int32_t* K, double beta, nmf_ctx** out);
+
+/* precision: see nmf_precision. order: see nmf_order. normalize != 0 divides
+ * each column of W by its l2 norm and scales H's row by it after every outer
+ * iteration (Sec. 4.1.2). kappa >= 0 minimises D_beta(V + kappa | WH + kappa)
+ * (Sec. 4.1.3). deterministic != 0 requests fixed-order reductions (every
+ * path here is deterministic; the flag is accepted for ABI stability).
+ * cuda_stream is a cudaStream_t or NULL. Resets scratch if precision changes. */
+nmf_status nmf_set_options(nmf_ctx* ctx, nmf_precision precision, nmf_order order,
+                           int normalize, double kappa, int deterministic,
+                           void* cuda_stream);
+
+/* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
+ * Algorithm 1) per outer iteration. */
+nmf_status nmf_set_subiterations(nmf_ctx* ctx, int32_t L);
+
+/* Borrows dense V (device, F x N row-major, leading dimension ldv >= N). */
+nmf_status nmf_set_dense(nmf_ctx* ctx, const void* V_dev, int64_t ldv);
+
+/* Borrows sparse V in CSR form (device arrays): rowptr has F + 1 entries,
+ * col and val have nnz entries; columns need not be sorted. Only beta = 1
+ * (KL) is supported on sparse data (count data, Sec. 4.4); zeros of V then
+ * contribute d_1(0 | [WH]_fn) = [WH]_fn to the objective. Precision must be
+ * NMF_FP32. kappa must be 0. The context builds a CSC copy in its scratch. */
+nmf_status nmf_set_csr(nmf_ctx* ctx, int64_t nnz, const int32_t* rowptr,
+                       const int32_t* col, const float* val);
+
+/* Borrows the factors (device): W F x K, H K x N, updated in place. */
+nmf_status nmf_set_factors(nmf_ctx* ctx, void* W_dev, void* H_dev);
+
+/* Batched contexts: V, W, H of every problem packed back to back, problem i
+ * starting at offset sum_{j<i} F_j N_j (V), sum_{j<i} F_j K_j (W),
+ * sum_{j<i} K_j N_j (H); each block row-major as above (ldv = N_i). */
+nmf_status nmf_batch_set_packed(nmf_ctx* ctx, const void* V_packed, void* W_packed,
+                                void* H_packed);
+
+/* Runs `iters` >= 1 outer iterations of JMM (Algorithm 2). If loss_out is not
+ * NULL it receives D_beta(V + kappa | Wt Ht + kappa) at the iterate entering
+ * the LAST iteration (computed inside that iteration's first sweep), and the
+ * call synchronises. For batched contexts loss_out is the sum over problems. */
+nmf_status nmf_step_joint(nmf_ctx* ctx, int32_t iters, double* loss_out);
+
+/* Same as nmf_step_joint for BMM (Algorithm 1). */
+nmf_status nmf_step_alternating(nmf_ctx* ctx, int32_t iters, double* loss_out);
+
+/* D_beta(V + kappa | WH + kappa) at the current factors (eq. obj_fct),
+ * accumulated in FP64; synchronises. */
+nmf_status nmf_loss(nmf_ctx* ctx, double* out_host);
+
+/* Gradient of D_beta(V + kappa | WH + kappa): gW = [(WH)^(b-2).(WH - V)] H^T
+ * (F x K) and gH = W^T [(WH)^(b-2).(WH - V)] (K x N), the terms of the KKT
+ * residuals (Sec. 4.1.5); equivalently the MU denominator minus numerator.
+ * gW_dev, gH_dev are caller-owned device buffers of the context's element
+ * type. If loss_out is not NULL it receives the loss at (W, H) and the call
+ * synchronises. */
+nmf_status nmf_grad(nmf_ctx* ctx, void* gW_dev, void* gH_dev, double* loss_out);
+
+/* KKT residuals res(W) = ||min{W, gW}||_1 / (FK), res(H) = ||min{H, gH}||_1 / (KN)
+ * (Sec. 4.1.5) at the current factors; synchronises. */
+nmf_status nmf_kkt(nmf_ctx* ctx, double* resW_host, double* resH_host);
+
+/* Batched contexts: per-problem losses of the last step that requested a
+ * loss (count doubles, host). */
+nmf_status nmf_batch_get_losses(nmf_ctx* ctx, double* out_host);
+
+/* Synchronises the stream and returns the sticky device status (NMF_OK or
+ * NMF_ENONFINITE / NMF_ETIMEOUT), restoring W and H on NMF_ENONFINITE. */
+nmf_status nmf_get_status(nmf_ctx* ctx);
+
+/* Host-buffer convenience for end-to-end use: copies V (F x N, packed), W and
+ * H from HOST memory (pinned memory is fastest) into context-owned device
+ * buffers, runs `iters` JMM iterations, copies W and H back and returns the
+ * loss as nmf_step_joint does. Single dense contexts only; the device
+ * buffers are allocated on first use and reused. */
+nmf_status nmf_step_joint_host(nmf_ctx* ctx, const void* V_host, void* W_host,
+                               void* H_host, int32_t iters, double* loss_out);
+
+/* Benchmark support. With enable != 0 the library records a CUDA event pair
+ * on the context's stream around every kernel it launches for this context
+ * and accumulates the durations per kernel name (adds two event records per
+ * launch; off by default). Launch counts are kept either way. */
+nmf_status nmf_set_timing(nmf_ctx* ctx, int enable);
+
+/* Timing record i (0-based, in order of first launch): kernel name (static
+ * string), number of launches and total device milliseconds since the last
+ * nmf_reset_timing. i = -1 returns the total launch count over all kernels in
+ * *launches (name "all", total_ms summed). Synchronises the stream.
+ * Returns NMF_EINVAL when i is past the last record. */
+nmf_status nmf_get_timing(nmf_ctx* ctx, int32_t i, const char** name, int64_t* launches,
+                          double* total_ms);
+
+/* Clears the timing records and launch counts. */
+nmf_status nmf_reset_timing(nmf_ctx* ctx);
+
+/* Frees the context and its scratch (not the borrowed buffers). NULL is a no-op. */
+void nmf_destroy(nmf_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* nmf_status_string(nmf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_GB300_H */

@@ -1,0 +1,820 @@
+// api.cu -- the C ABI declared in include/nmf.h: contexts, scratch planning,
+// and the drivers that compose the sweep kernels into Algorithm 1 (BMM) and
+// Algorithm 2 (JMM).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "nmf.h"
+#include "tc_dense.h"
+
+using namespace nmf;
+
+struct nmf_ctx {
+  bool batched = false;
+  int count = 1;
+  std::vector<int64_t> F, N;
+  std::vector<int> K;
+  double beta = 1.0;
+  nmf_precision prec = NMF_FP32;
+  nmf_order order = NMF_W_FIRST;
+  int normalize = 1;
+  double kappa = 0.0;
+  int deterministic = 1;
+  cudaStream_t stream = nullptr;
+  int L = 1;
+  // single-problem data
+  const void* V = nullptr;
+  int64_t ldv = 0;
+  void* W = nullptr;
+  void* H = nullptr;
+  // batched packed data
+  const void* Vp = nullptr;
+  void* Wp = nullptr;
+  void* Hp = nullptr;
+  // sparse data
+  bool sparse = false;
+  int64_t nnz = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const float* val = nullptr;
+  bool cscBuilt = false;
+  // device state
+  bool prepared = false;
+  bool tableDirty = true;
+  std::vector<void*> allocs;
+  Plan<float> pf;
+  Plan<double> pd;
+  std::vector<Prob<float>> hpf;
+  std::vector<Prob<double>> hpd;
+  int* d_status = nullptr;
+  double* d_lossPart = nullptr;
+  double* d_lossOut = nullptr;
+  double* h_pinned = nullptr;  // count losses + status + kkt
+  int lossPrefix = 0;          // 0: row-sweep blocks, 1: column-sweep blocks
+  bool lossValid = false;
+  std::vector<double> lastLosses;
+  void* tildeW = nullptr;      // packed W at the start of the iteration
+  void* tildeH = nullptr;
+  size_t elemsW = 0, elemsH = 0, elemsV = 0;
+  void* d_gW = nullptr;
+  void* d_gH = nullptr;
+  double* d_kkt = nullptr;
+  void* stageV = nullptr;
+  void* stageW = nullptr;
+  void* stageH = nullptr;
+  TcState* tc = nullptr;
+  SparseKL sp;
+  Timer timer;
+  int sms = 148;
+};
+
+namespace {
+
+size_t esize(const nmf_ctx* c) { return c->prec == NMF_FP64 ? 8 : 4; }
+
+nmf_status cu(cudaError_t e) { return e == cudaSuccess ? NMF_OK : NMF_ECUDA; }
+
+#define NMF_TRY(x)                     \
+  do {                                 \
+    nmf_status _s = (x);               \
+    if (_s != NMF_OK) return _s;       \
+  } while (0)
+#define NMF_CU(x) NMF_TRY(cu(x))
+
+void free_all(nmf_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  c->h_pinned = nullptr;
+  if (c->tc) tc_destroy(c->tc);
+  c->tc = nullptr;
+  c->prepared = false;
+  c->tableDirty = true;
+  c->cscBuilt = false;
+  c->d_gW = c->d_gH = nullptr;
+  c->d_kkt = nullptr;
+  c->stageV = c->stageW = c->stageH = nullptr;
+  c->sp = SparseKL();
+}
+
+nmf_status dalloc(nmf_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return NMF_ENOMEM;
+  }
+  c->allocs.push_back(*p);
+  return NMF_OK;
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct Tiling {
+  int rowTilesF, S, colTilesN, R;
+  int64_t chunkN, chunkF;
+};
+
+// Splits of the two sweeps: enough blocks to fill the GPU twice over for a
+// single problem; for batches, chunks capped so no block walks a whole long
+// row or column of a big member while small members finish early.
+Tiling tiling(int64_t F, int64_t N, int sms, bool batched) {
+  Tiling t;
+  t.rowTilesF = (int)cdiv(F, BF);
+  t.colTilesN = (int)cdiv(N, BN);
+  const int64_t nTiles = cdiv(N, BN), fTiles = cdiv(F, BF);
+  const int64_t target = 2LL * sms;
+  int64_t S = batched ? 1 : std::max<int64_t>(1, cdiv(target, t.rowTilesF));
+  S = std::max<int64_t>(S, cdiv(nTiles, 64));
+  S = std::min<int64_t>(S, nTiles);
+  t.chunkN = cdiv(nTiles, S) * BN;
+  t.S = (int)cdiv(N, t.chunkN);
+  int64_t R = batched ? 1 : std::max<int64_t>(1, cdiv(target, t.colTilesN));
+  R = std::max<int64_t>(R, cdiv(fTiles, 64));
+  R = std::min<int64_t>(R, fTiles);
+  t.chunkF = cdiv(fTiles, R) * BF;
+  t.R = (int)cdiv(F, t.chunkF);
+  return t;
+}
+
+bool data_ready(const nmf_ctx* c) {
+  if (c->batched) return c->Vp && c->Wp && c->Hp;
+  if (c->sparse) return c->rowptr && c->W && c->H;
+  return c->V && c->W && c->H;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename T>
+nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
+  const int cnt = c->count;
+  probs.assign(cnt, Prob<T>());
+  std::vector<int> pr(cnt + 1), pc(cnt + 1), pw(cnt + 1), ph(cnt + 1), pk(cnt + 1);
+  pr[0] = pc[0] = pw[0] = ph[0] = pk[0] = 0;
+  // scratch bytes per problem (excluding the packed tilde buffers)
+  std::vector<size_t> off(cnt + 1, 0);
+  std::vector<Tiling> tl(cnt);
+  int maxK = 0;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t F = c->F[i], N = c->N[i];
+    const int K = c->K[i];
+    maxK = std::max(maxK, K);
+    tl[i] = tiling(F, N, c->sms, c->batched);
+    const size_t FK = (size_t)F * K, KN = (size_t)K * N;
+    size_t bytes = 0;
+    bytes += align256(sizeof(T) * FK) * 2;                         // chiW1, chiW2
+    bytes += align256(sizeof(T) * KN) * 2;                         // chiH1, chiH2
+    bytes += align256(sizeof(T) * FK * 2 * tl[i].S);               // rowPart
+    bytes += align256(sizeof(T) * KN * 2 * tl[i].R);               // colPart
+    bytes += align256(sizeof(T) * K);                              // norms
+    off[i + 1] = off[i] + bytes;
+    pr[i + 1] = pr[i] + tl[i].rowTilesF * tl[i].S;
+    pc[i + 1] = pc[i] + tl[i].colTilesN * tl[i].R;
+    pw[i + 1] = pw[i] + (int)cdiv((int64_t)FK, EW);
+    ph[i + 1] = ph[i] + (int)cdiv((int64_t)KN, EW);
+    pk[i + 1] = pk[i] + K;
+  }
+  void* scratch = nullptr;
+  NMF_TRY(dalloc(c, &scratch, off[cnt]));
+  NMF_TRY(dalloc(c, &c->tildeW, sizeof(T) * c->elemsW));
+  NMF_TRY(dalloc(c, &c->tildeH, sizeof(T) * c->elemsH));
+  size_t oW = 0, oH = 0, oV = 0;
+  for (int i = 0; i < cnt; ++i) {
+    Prob<T>& P = probs[i];
+    const int64_t F = c->F[i], N = c->N[i];
+    const int K = c->K[i];
+    const size_t FK = (size_t)F * K, KN = (size_t)K * N;
+    char* base = static_cast<char*>(scratch) + off[i];
+    auto take = [&](size_t bytes) { T* p = reinterpret_cast<T*>(base); base += align256(bytes); return p; };
+    P.chiW1 = take(sizeof(T) * FK);
+    P.chiW2 = take(sizeof(T) * FK);
+    P.chiH1 = take(sizeof(T) * KN);
+    P.chiH2 = take(sizeof(T) * KN);
+    P.rowPart = take(sizeof(T) * FK * 2 * tl[i].S);
+    P.colPart = take(sizeof(T) * KN * 2 * tl[i].R);
+    P.norms = take(sizeof(T) * K);
+    P.Wt = static_cast<T*>(c->tildeW) + oW;
+    P.Ht = static_cast<T*>(c->tildeH) + oH;
+    P.F = F; P.N = N; P.K = K;
+    P.S = tl[i].S; P.R = tl[i].R;
+    P.rowTilesF = tl[i].rowTilesF; P.colTilesN = tl[i].colTilesN;
+    P.chunkN = tl[i].chunkN; P.chunkF = tl[i].chunkF;
+    P.V = nullptr; P.W = nullptr; P.H = nullptr;
+    P.ldv = c->batched ? N : c->ldv;
+    oW += FK; oH += KN; oV += (size_t)F * N;
+  }
+  void* d = nullptr;
+  NMF_TRY(dalloc(c, &d, sizeof(Prob<T>) * cnt));
+  pl.d_probs = static_cast<Prob<T>*>(d);
+  pl.count = cnt;
+  pl.maxK = maxK;
+  int* tabs = nullptr;
+  NMF_TRY(dalloc(c, reinterpret_cast<void**>(&tabs), sizeof(int) * 5 * (cnt + 1)));
+  std::vector<int> all;
+  all.insert(all.end(), pr.begin(), pr.end());
+  all.insert(all.end(), pc.begin(), pc.end());
+  all.insert(all.end(), pw.begin(), pw.end());
+  all.insert(all.end(), ph.begin(), ph.end());
+  all.insert(all.end(), pk.begin(), pk.end());
+  NMF_CU(cudaMemcpy(tabs, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+  pl.d_prefRow = tabs; pl.totRow = pr[cnt];
+  pl.d_prefCol = tabs + (cnt + 1); pl.totCol = pc[cnt];
+  pl.d_prefW = tabs + 2 * (cnt + 1); pl.totW = pw[cnt];
+  pl.d_prefH = tabs + 3 * (cnt + 1); pl.totH = ph[cnt];
+  pl.d_prefK = tabs + 4 * (cnt + 1); pl.totK = pk[cnt];
+  const size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
+  NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
+  return NMF_OK;
+}
+
+template <typename T>
+nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
+  size_t oW = 0, oH = 0, oV = 0;
+  for (int i = 0; i < c->count; ++i) {
+    Prob<T>& P = probs[i];
+    if (c->batched) {
+      P.V = static_cast<const T*>(c->Vp) + oV;
+      P.W = static_cast<T*>(c->Wp) + oW;
+      P.H = static_cast<T*>(c->Hp) + oH;
+      P.ldv = P.N;
+    } else {
+      P.V = static_cast<const T*>(c->V);
+      P.W = static_cast<T*>(c->W);
+      P.H = static_cast<T*>(c->H);
+      P.ldv = c->ldv;
+    }
+    oW += (size_t)P.F * P.K; oH += (size_t)P.K * P.N; oV += (size_t)P.F * P.N;
+  }
+  NMF_CU(cudaMemcpyAsync(pl.d_probs, probs.data(), sizeof(Prob<T>) * c->count,
+                         cudaMemcpyHostToDevice, c->stream));
+  c->tableDirty = false;
+  return NMF_OK;
+}
+
+// Allocates the context's scratch on first use (or after a precision change),
+// then uploads the problem table if data pointers changed. Anything allocated
+// after the first prepare() (staging, gradient scratch) survives later calls.
+nmf_status prepare(nmf_ctx* c) {
+  if (!c->prepared) {
+    free_all(c);
+    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int)));
+    NMF_CU(cudaMemset(c->d_status, 0, sizeof(int)));
+    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossOut), sizeof(double) * (c->count + 4)));
+    if (cudaMallocHost(&c->h_pinned, sizeof(double) * (c->count + 8)) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_pinned = nullptr;
+      return NMF_ENOMEM;
+    }
+    if (c->sparse) {
+      // sparse KL path has its own scratch (sparse_kl.cu)
+      SparseKL& s = c->sp;
+      s.F = c->F[0]; s.N = c->N[0]; s.K = c->K[0]; s.nnz = c->nnz;
+      const int K = s.K;
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.rowidx), sizeof(int32_t) * std::max<int64_t>(1, s.nnz)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.colptr), sizeof(int32_t) * (s.N + 1)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.cscRow), sizeof(int32_t) * std::max<int64_t>(1, s.nnz)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.cscPos), sizeof(int64_t) * std::max<int64_t>(1, s.nnz)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.a), sizeof(float) * std::max<int64_t>(1, s.nnz)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.Wt), sizeof(float) * s.F * K));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.Ht), sizeof(float) * s.N * K * 2));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.colsumW), sizeof(float) * K * 4));
+      s.rowsumH = s.colsumW + K;
+      s.chi = s.colsumW + 2 * K;
+      s.lossBlocks = (int)std::max<int64_t>(cdiv(s.F, 8), cdiv(s.N, 32));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.lossPart), sizeof(double) * (s.lossBlocks + 64)));
+      NMF_TRY(dalloc(c, reinterpret_cast<void**>(&s.sums), sizeof(double) * 64));
+      c->tildeW = s.Wt;
+      c->tildeH = s.Ht;  // H tilde, row-major K x N (first half of the Ht buffer)
+      c->prepared = true;
+      return NMF_OK;
+    }
+    // TF32/BF16 contexts also get the float plan: their loss, gradient and
+    // alternating baseline run on the FP32 SIMT kernels.
+    if (c->prec == NMF_FP64) NMF_TRY(build_plan<double>(c, c->pd, c->hpd));
+    else NMF_TRY(build_plan<float>(c, c->pf, c->hpf));
+    c->prepared = true;
+    c->tableDirty = true;
+  }
+  if (c->tableDirty && !c->sparse && data_ready(c)) {
+    if (c->prec == NMF_FP64) NMF_TRY(upload_table<double>(c, c->pd, c->hpd));
+    else NMF_TRY(upload_table<float>(c, c->pf, c->hpf));
+  }
+  return NMF_OK;
+}
+
+
+BetaParams beta_params(const nmf_ctx* c) {
+  BetaParams bp;
+  bp.beta = c->beta;
+  bp.gamma = gamma_of(c->beta);
+  bp.kappa = c->kappa;
+  bp.kind = beta_kind(c->beta);
+  return bp;
+}
+
+// One or more outer iterations of Algorithm 2 (joint) or Algorithm 1 (alternating).
+template <typename T>
+nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLoss) {
+  const BetaParams bp = beta_params(c);
+  cudaStream_t st = c->stream;
+  int* status = c->d_status;
+  double* lp = c->d_lossPart;
+  const bool wfirst = c->order == NMF_W_FIRST ||
+                      (c->order == NMF_ORDER_AUTO && c->F[0] >= c->N[0]);
+  const int L = c->L;
+  const int C = SWEEP_CONTRACT;
+  for (int it = 0; it < iters; ++it) {
+    const bool lossHere = wantLoss && it == iters - 1;
+    const int CL = C | (lossHere ? SWEEP_LOSS : 0);
+    NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
+    if (joint) {
+      for (int l = 1; l <= L; ++l) {
+        const int f1 = l == 1 ? CL : C;
+        if (wfirst) {
+          NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1, bp, lp, status, st); }));
+          NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 1, bp, nullptr, status, st); }));
+          NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_TILDE, SEL_TILDE, OP_CHI, C, bp, lp, status, st); }));
+          NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, l < L, bp, nullptr, status, st); }));
+        } else {
+          NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1, bp, lp, status, st); }));
+          NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 1, bp, nullptr, status, st); }));
+          NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_TILDE, SEL_TILDE, OP_CHI, C, bp, lp, status, st); }));
+          NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, l < L, bp, nullptr, status, st); }));
+        }
+      }
+    } else {
+      for (int half = 0; half < 2; ++half) {
+        const bool doW = (half == 0) == wfirst;
+        for (int l = 1; l <= L; ++l) {
+          const int fl = (half == 0 && l == 1) ? CL : C;
+          if (doW) {
+            NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, lp, status, st); }));
+            NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_CUR, 0, bp, nullptr, status, st); }));
+          } else {
+            NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, lp, status, st); }));
+            NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_CUR, 0, bp, nullptr, status, st); }));
+          }
+        }
+      }
+    }
+    if (c->normalize) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
+  }
+  if (wantLoss) c->lossPrefix = wfirst ? 0 : 1;
+  return NMF_OK;
+}
+
+nmf_status finalize_loss_dense(nmf_ctx* c) {
+  const int* pref = nullptr;
+  if (c->prec == NMF_FP64) pref = c->lossPrefix == 0 ? c->pd.d_prefRow : c->pd.d_prefCol;
+  else pref = c->lossPrefix == 0 ? c->pf.d_prefRow : c->pf.d_prefCol;
+  return cu(timed(&c->timer, c->stream, "loss_finalize", 1, [&] {
+    return launch_loss_finalize(pref, c->count, c->d_lossPart, c->d_lossOut, c->stream);
+  }));
+}
+
+// Synchronises; on a device-side non-finite flag restores W, H from the tilde copies.
+nmf_status sync_and_check(nmf_ctx* c, bool readLoss, double* loss_out) {
+  const int cnt = c->count;
+  if (readLoss)
+    NMF_CU(cudaMemcpyAsync(c->h_pinned, c->d_lossOut, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  int* hs = reinterpret_cast<int*>(c->h_pinned + cnt + 1);
+  NMF_CU(cudaMemcpyAsync(hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  NMF_CU(cudaStreamSynchronize(c->stream));
+  if (*hs != 0) {
+    const size_t es = c->sparse ? 4 : esize(c);
+    void* W = c->batched ? c->Wp : c->W;
+    void* H = c->batched ? c->Hp : c->H;
+    NMF_CU(cudaMemcpyAsync(W, c->tildeW, es * c->elemsW, cudaMemcpyDeviceToDevice, c->stream));
+    NMF_CU(cudaMemcpyAsync(H, c->tildeH, es * c->elemsH, cudaMemcpyDeviceToDevice, c->stream));
+    NMF_CU(cudaStreamSynchronize(c->stream));
+    return (nmf_status)*hs;
+  }
+  if (readLoss) {
+    c->lastLosses.assign(c->h_pinned, c->h_pinned + cnt);
+    c->lossValid = true;
+    if (loss_out) {
+      double s = 0.0;
+      for (int i = 0; i < cnt; ++i) s += c->h_pinned[i];
+      *loss_out = s;
+    }
+  }
+  return NMF_OK;
+}
+
+// Sparse contexts: binds the caller's CSR arrays and builds the CSC copy once
+// (every sparse entry point calls this after prepare()).
+nmf_status ensure_sparse(nmf_ctx* c) {
+  if (c->cscBuilt) return NMF_OK;
+  c->sp.rowptr = c->rowptr;
+  c->sp.col = c->col;
+  c->sp.val = c->val;
+  void* tmp = nullptr;
+  const size_t tb = sparse_csc_tmp_bytes(c->sp.F, c->sp.N, c->nnz);
+  NMF_TRY(dalloc(c, &tmp, tb));
+  const cudaError_t be = sparse_build_csc(c->sp, tmp, tb, c->stream);
+  if (be == cudaErrorInvalidValue) return NMF_EINVAL;  // malformed CSR arrays, nothing was indexed
+  NMF_CU(be);
+  c->cscBuilt = true;
+  return NMF_OK;
+}
+
+nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
+  if (!c || iters < 1) return NMF_EINVAL;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  NMF_TRY(prepare(c));
+  const bool wantLoss = loss_out != nullptr;
+  if (c->sparse) {
+    NMF_TRY(ensure_sparse(c));
+    const bool hfirst = c->order == NMF_H_FIRST || (c->order == NMF_ORDER_AUTO && c->F[0] < c->N[0]);
+    for (int it = 0; it < iters; ++it) {
+      const bool lossHere = wantLoss && it == iters - 1;
+      NMF_CU(sparse_step(c->sp, static_cast<float*>(c->W), static_cast<float*>(c->H), joint, hfirst,
+                         lossHere, c->normalize != 0, c->d_status, &c->timer, c->stream));
+    }
+    if (wantLoss) NMF_CU(cudaMemcpyAsync(c->d_lossOut, c->sp.sums, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (!wantLoss) return NMF_OK;
+    return sync_and_check(c, true, loss_out);
+  }
+  if (c->prec == NMF_TF32 || c->prec == NMF_BF16) {
+    if (c->batched || c->L != 1 || !joint) return NMF_EUNSUPPORTED;
+    if (!c->tc) {
+      nmf_status s = tc_create(&c->tc, c->F[0], c->N[0], c->K[0], c->beta, c->kappa,
+                               c->prec == NMF_BF16, c->sms);
+      if (s != NMF_OK) return s;
+    }
+    const bool hfirst = c->order != NMF_W_FIRST;
+    NMF_TRY(tc_step(c->tc, static_cast<const float*>(c->V), c->ldv, static_cast<float*>(c->W),
+                    static_cast<float*>(c->H), iters, wantLoss, c->normalize != 0, hfirst,
+                    c->d_status, c->d_lossOut, &c->timer, c->stream));
+    if (!wantLoss) return NMF_OK;
+    return sync_and_check(c, true, loss_out);
+  }
+  if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss));
+  else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss));
+  if (!wantLoss) return NMF_OK;
+  NMF_TRY(finalize_loss_dense(c));
+  return sync_and_check(c, true, loss_out);
+}
+
+bool valid_beta(double b) { return std::isfinite(b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Loss finalisation kernel: per problem, fixed-order sum of its block partials.
+// ---------------------------------------------------------------------------
+namespace nmf {
+__global__ void loss_finalize_kernel(const int* __restrict__ prefix, const double* __restrict__ part,
+                                     double* __restrict__ out) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int b = prefix[i] + threadIdx.x; b < prefix[i + 1]; b += blockDim.x) s += part[b];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[i] = s;
+}
+cudaError_t launch_loss_finalize(const int* d_prefix, int count, const double* lossPart, double* out,
+                                 cudaStream_t st) {
+  loss_finalize_kernel<<<count, 256, 0, st>>>(d_prefix, lossPart, out);
+  return cudaGetLastError();
+}
+}  // namespace nmf
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+nmf_status nmf_create(int64_t F, int64_t N, int32_t K, double beta, nmf_ctx** out) {
+  if (!out) return NMF_EINVAL;
+  *out = nullptr;
+  if (F < 1 || N < 1 || K < 1 || !valid_beta(beta)) return NMF_EINVAL;
+  if (K > KMAX) return NMF_EUNSUPPORTED;
+  if (F > (int64_t)1 << 31 || N > (int64_t)1 << 31) return NMF_EINVAL;
+  nmf_ctx* c = new (std::nothrow) nmf_ctx();
+  if (!c) return NMF_ENOMEM;
+  c->F = {F}; c->N = {N}; c->K = {K};
+  c->beta = beta;
+  c->elemsW = (size_t)F * K; c->elemsH = (size_t)K * N; c->elemsV = (size_t)F * N;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  *out = c;
+  return NMF_OK;
+}
+
+nmf_status nmf_batch_create(int32_t count, const int64_t* F, const int64_t* N, const int32_t* K,
+                            double beta, nmf_ctx** out) {
+  if (!out) return NMF_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !F || !N || !K || !valid_beta(beta)) return NMF_EINVAL;
+  nmf_ctx* c = new (std::nothrow) nmf_ctx();
+  if (!c) return NMF_ENOMEM;
+  c->batched = true;
+  c->count = count;
+  c->beta = beta;
+  for (int i = 0; i < count; ++i) {
+    if (F[i] < 1 || N[i] < 1 || K[i] < 1 || K[i] > KMAX) { delete c; return K[i] > KMAX ? NMF_EUNSUPPORTED : NMF_EINVAL; }
+    c->F.push_back(F[i]); c->N.push_back(N[i]); c->K.push_back(K[i]);
+    c->elemsW += (size_t)F[i] * K[i]; c->elemsH += (size_t)K[i] * N[i]; c->elemsV += (size_t)F[i] * N[i];
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  *out = c;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_options(nmf_ctx* c, nmf_precision precision, nmf_order order, int normalize,
+                           double kappa, int deterministic, void* cuda_stream) {
+  if (!c) return NMF_EINVAL;
+  if (precision < NMF_FP64 || precision > NMF_BF16) return NMF_EINVAL;
+  if (order < NMF_W_FIRST || order > NMF_ORDER_AUTO) return NMF_EINVAL;
+  if (!(kappa >= 0.0) || !std::isfinite(kappa)) return NMF_EINVAL;
+  if (c->sparse && (precision != NMF_FP32 || kappa != 0.0)) return NMF_EINVAL;
+  if (precision != c->prec && c->prepared) { cudaStreamSynchronize(c->stream); free_all(c); }
+  if (c->tc && (kappa != c->kappa)) { tc_destroy(c->tc); c->tc = nullptr; }
+  c->prec = precision;
+  c->order = order;
+  c->normalize = normalize ? 1 : 0;
+  c->kappa = kappa;
+  c->deterministic = deterministic ? 1 : 0;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return NMF_OK;
+}
+
+nmf_status nmf_set_subiterations(nmf_ctx* c, int32_t L) {
+  if (!c || L < 1) return NMF_EINVAL;
+  if (c->sparse && L != 1) return NMF_EUNSUPPORTED;
+  c->L = L;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_dense(nmf_ctx* c, const void* V_dev, int64_t ldv) {
+  if (!c || !V_dev || c->batched || c->sparse || ldv < c->N[0]) return NMF_EINVAL;
+  c->V = V_dev;
+  c->ldv = ldv;
+  c->tableDirty = true;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_csr(nmf_ctx* c, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                       const float* val) {
+  if (!c || c->batched || nnz < 0 || (nnz > 0 && (!col || !val)) || !rowptr) return NMF_EINVAL;
+  if (c->beta != 1.0 || c->kappa != 0.0 || c->prec != NMF_FP32 || c->L != 1) return NMF_EINVAL;
+  if (nnz >= ((int64_t)1 << 31)) return NMF_EUNSUPPORTED;
+  if (c->V) return NMF_EINVAL;
+  if (c->prepared) { cudaStreamSynchronize(c->stream); free_all(c); }
+  c->sparse = true;
+  c->nnz = nnz;
+  c->rowptr = rowptr; c->col = col; c->val = val;
+  c->cscBuilt = false;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_factors(nmf_ctx* c, void* W_dev, void* H_dev) {
+  if (!c || !W_dev || !H_dev || c->batched) return NMF_EINVAL;
+  c->W = W_dev;
+  c->H = H_dev;
+  c->tableDirty = true;
+  if (c->d_status) {
+    if (cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) != cudaSuccess) return NMF_ECUDA;
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_batch_set_packed(nmf_ctx* c, const void* V_packed, void* W_packed, void* H_packed) {
+  if (!c || !c->batched || !V_packed || !W_packed || !H_packed) return NMF_EINVAL;
+  c->Vp = V_packed; c->Wp = W_packed; c->Hp = H_packed;
+  c->tableDirty = true;
+  if (c->d_status) {
+    if (cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) != cudaSuccess) return NMF_ECUDA;
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_step_joint(nmf_ctx* c, int32_t iters, double* loss_out) {
+  return step(c, true, iters, loss_out);
+}
+
+nmf_status nmf_step_alternating(nmf_ctx* c, int32_t iters, double* loss_out) {
+  if (c && (c->prec == NMF_TF32 || c->prec == NMF_BF16) && !c->sparse) {
+    // the alternating baseline runs on the SIMT FP32 kernels for tensor-core precisions
+    nmf_precision keep = c->prec;
+    c->prec = NMF_FP32;
+    nmf_status s = step(c, false, iters, loss_out);
+    c->prec = keep;
+    return s;
+  }
+  return step(c, false, iters, loss_out);
+}
+
+nmf_status nmf_loss(nmf_ctx* c, double* out_host) {
+  if (!c || !out_host) return NMF_EINVAL;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  nmf_precision keep = c->prec;
+  if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
+  nmf_status s = prepare(c);
+  if (s == NMF_OK && c->sparse) s = ensure_sparse(c);
+  if (s == NMF_OK) {
+    if (c->sparse) {
+      s = cu(sparse_loss(c->sp, static_cast<const float*>(c->W), static_cast<const float*>(c->H),
+                         c->d_lossOut, c->stream));
+    } else {
+      const BetaParams bp = beta_params(c);
+      if (c->prec == NMF_FP64)
+        s = cu(launch_row_sweep<double>(c->pd, SEL_CUR, SEL_CUR, OP_SELF, SWEEP_LOSS, bp, c->d_lossPart, c->d_status, c->stream));
+      else
+        s = cu(launch_row_sweep<float>(c->pf, SEL_CUR, SEL_CUR, OP_SELF, SWEEP_LOSS, bp, c->d_lossPart, c->d_status, c->stream));
+      c->lossPrefix = 0;
+      if (s == NMF_OK) s = finalize_loss_dense(c);
+    }
+    if (s == NMF_OK) s = sync_and_check(c, true, out_host);
+  }
+  c->prec = keep;
+  return s;
+}
+
+nmf_status nmf_grad(nmf_ctx* c, void* gW_dev, void* gH_dev, double* loss_out) {
+  if (!c || !gW_dev || !gH_dev) return NMF_EINVAL;
+  if (c->batched) return NMF_EUNSUPPORTED;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  nmf_precision keep = c->prec;
+  if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
+  nmf_status s = prepare(c);
+  if (s == NMF_OK && c->sparse) s = ensure_sparse(c);
+  const bool wantLoss = loss_out != nullptr;
+  if (s == NMF_OK) {
+    if (c->sparse) {
+      s = cu(sparse_grad(c->sp, static_cast<const float*>(c->W), static_cast<const float*>(c->H),
+                         static_cast<float*>(gW_dev), static_cast<float*>(gH_dev), c->stream));
+      if (s == NMF_OK && wantLoss)
+        s = cu(sparse_loss_finalize(c->sp, static_cast<const float*>(c->W), static_cast<const float*>(c->H),
+                                    c->d_lossOut, c->stream));
+    } else {
+      const BetaParams bp = beta_params(c);
+      const int fl = SWEEP_CONTRACT | (wantLoss ? SWEEP_LOSS : 0);
+      if (c->prec == NMF_FP64) {
+        s = cu(launch_row_sweep<double>(c->pd, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, c->d_lossPart, c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_rows_epilogue<double>(c->pd, EPI_GRAD, SEL_CUR, 0, bp, static_cast<double*>(gW_dev), c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_col_sweep<double>(c->pd, SEL_CUR, SEL_CUR, OP_SELF, SWEEP_CONTRACT, bp, c->d_lossPart, c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_cols_epilogue<double>(c->pd, EPI_GRAD, SEL_CUR, 0, bp, static_cast<double*>(gH_dev), c->d_status, c->stream));
+      } else {
+        s = cu(launch_row_sweep<float>(c->pf, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, c->d_lossPart, c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_rows_epilogue<float>(c->pf, EPI_GRAD, SEL_CUR, 0, bp, static_cast<float*>(gW_dev), c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_col_sweep<float>(c->pf, SEL_CUR, SEL_CUR, OP_SELF, SWEEP_CONTRACT, bp, c->d_lossPart, c->d_status, c->stream));
+        if (s == NMF_OK) s = cu(launch_cols_epilogue<float>(c->pf, EPI_GRAD, SEL_CUR, 0, bp, static_cast<float*>(gH_dev), c->d_status, c->stream));
+      }
+      c->lossPrefix = 0;
+      if (s == NMF_OK && wantLoss) s = finalize_loss_dense(c);
+    }
+    if (s == NMF_OK && wantLoss) s = sync_and_check(c, true, loss_out);
+  }
+  c->prec = keep;
+  return s;
+}
+
+nmf_status nmf_kkt(nmf_ctx* c, double* resW, double* resH) {
+  if (!c || !resW || !resH) return NMF_EINVAL;
+  if (c->batched) return NMF_EUNSUPPORTED;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  nmf_precision keep = c->prec;
+  if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
+  nmf_status s = prepare(c);
+  const size_t es = c->sparse ? 4 : esize(c);
+  if (s == NMF_OK && !c->d_gW) {
+    s = dalloc(c, &c->d_gW, es * c->elemsW);
+    if (s == NMF_OK) s = dalloc(c, &c->d_gH, es * c->elemsH);
+    if (s == NMF_OK) s = dalloc(c, reinterpret_cast<void**>(&c->d_kkt), sizeof(double) * 2);
+  }
+  if (s == NMF_OK) {
+    c->prec = keep;
+    s = nmf_grad(c, c->d_gW, c->d_gH, nullptr);
+    if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
+  }
+  if (s == NMF_OK) {
+    if (c->prec == NMF_FP64)
+      s = cu(launch_kkt<double>(static_cast<double*>(c->W), static_cast<double*>(c->d_gW), c->elemsW,
+                                static_cast<double*>(c->H), static_cast<double*>(c->d_gH), c->elemsH, c->d_kkt, c->stream));
+    else
+      s = cu(launch_kkt<float>(static_cast<float*>(c->W), static_cast<float*>(c->d_gW), c->elemsW,
+                               static_cast<float*>(c->H), static_cast<float*>(c->d_gH), c->elemsH, c->d_kkt, c->stream));
+  }
+  if (s == NMF_OK) {
+    s = cu(cudaMemcpyAsync(c->h_pinned + c->count + 2, c->d_kkt, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    if (s == NMF_OK) s = sync_and_check(c, false, nullptr);
+    if (s == NMF_OK) {
+      *resW = c->h_pinned[c->count + 2] / (double)c->elemsW;
+      *resH = c->h_pinned[c->count + 3] / (double)c->elemsH;
+    }
+  }
+  c->prec = keep;
+  return s;
+}
+
+nmf_status nmf_batch_get_losses(nmf_ctx* c, double* out_host) {
+  if (!c || !out_host) return NMF_EINVAL;
+  if (!c->lossValid) return NMF_ENOTREADY;
+  std::copy(c->lastLosses.begin(), c->lastLosses.end(), out_host);
+  return NMF_OK;
+}
+
+nmf_status nmf_get_status(nmf_ctx* c) {
+  if (!c) return NMF_EINVAL;
+  if (!c->prepared) return NMF_OK;
+  return sync_and_check(c, false, nullptr);
+}
+
+nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, void* H_host,
+                               int32_t iters, double* loss_out) {
+  if (!c || !V_host || !W_host || !H_host || iters < 1) return NMF_EINVAL;
+  if (c->batched || c->sparse) return NMF_EUNSUPPORTED;
+  const size_t es = esize(c);
+  NMF_TRY(prepare(c));  // scratch first: a first-time prepare() must not free the staging buffers
+  if (!c->stageV) {
+    nmf_status s = dalloc(c, &c->stageV, es * c->elemsV);
+    if (s == NMF_OK) s = dalloc(c, &c->stageW, es * c->elemsW);
+    if (s == NMF_OK) s = dalloc(c, &c->stageH, es * c->elemsH);
+    if (s != NMF_OK) return s;
+  }
+  const void* keepV = c->V; void* keepW = c->W; void* keepH = c->H; int64_t keepLd = c->ldv;
+  NMF_CU(cudaMemcpyAsync(c->stageV, V_host, es * c->elemsV, cudaMemcpyHostToDevice, c->stream));
+  NMF_CU(cudaMemcpyAsync(c->stageW, W_host, es * c->elemsW, cudaMemcpyHostToDevice, c->stream));
+  NMF_CU(cudaMemcpyAsync(c->stageH, H_host, es * c->elemsH, cudaMemcpyHostToDevice, c->stream));
+  c->V = c->stageV; c->W = c->stageW; c->H = c->stageH; c->ldv = c->N[0];
+  c->tableDirty = true;
+  nmf_status s = step(c, true, iters, loss_out);
+  if (s == NMF_OK || s == NMF_ENONFINITE) {
+    nmf_status s2 = cu(cudaMemcpyAsync(W_host, c->stageW, es * c->elemsW, cudaMemcpyDeviceToHost, c->stream));
+    if (s2 == NMF_OK) s2 = cu(cudaMemcpyAsync(H_host, c->stageH, es * c->elemsH, cudaMemcpyDeviceToHost, c->stream));
+    if (s2 == NMF_OK) s2 = cu(cudaStreamSynchronize(c->stream));
+    if (s == NMF_OK) s = s2;
+  }
+  c->V = keepV; c->W = keepW; c->H = keepH; c->ldv = keepLd;
+  c->tableDirty = true;
+  return s;
+}
+
+nmf_status nmf_set_timing(nmf_ctx* c, int enable) {
+  if (!c) return NMF_EINVAL;
+  c->timer.on = enable != 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_get_timing(nmf_ctx* c, int32_t i, const char** name, int64_t* launches, double* total_ms) {
+  if (!c || !name || !launches || !total_ms) return NMF_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NMF_ECUDA;
+  c->timer.resolve();
+  if (i == -1) {
+    *name = "all";
+    *launches = c->timer.total;
+    double s = 0.0;
+    for (auto& r : c->timer.recs) s += r.ms;
+    *total_ms = s;
+    return NMF_OK;
+  }
+  if (i < 0 || i >= (int32_t)c->timer.recs.size()) return NMF_EINVAL;
+  *name = c->timer.recs[i].name;
+  *launches = c->timer.recs[i].launches;
+  *total_ms = c->timer.recs[i].ms;
+  return NMF_OK;
+}
+
+nmf_status nmf_reset_timing(nmf_ctx* c) {
+  if (!c) return NMF_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NMF_ECUDA;
+  c->timer.reset();
+  return NMF_OK;
+}
+
+void nmf_destroy(nmf_ctx* c) {
+  if (!c) return;
+  if (c->prepared) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+const char* nmf_status_string(nmf_status s) {
+  switch (s) {
+    case NMF_OK: return "NMF_OK";
+    case NMF_EINVAL: return "NMF_EINVAL: invalid argument";
+    case NMF_ENOMEM: return "NMF_ENOMEM: allocation failed";
+    case NMF_ECUDA: return "NMF_ECUDA: CUDA runtime error";
+    case NMF_ENONFINITE: return "NMF_ENONFINITE: non-finite value in an update";
+    case NMF_ETIMEOUT: return "NMF_ETIMEOUT: device wait timed out";
+    case NMF_EUNSUPPORTED: return "NMF_EUNSUPPORTED: not supported by this build";
+    case NMF_ENOTREADY: return "NMF_ENOTREADY: data or factors not set";
+  }
+  return "unknown nmf_status";
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// common.cuh -- device-side building blocks shared by the CUDA kernels of libnmf.
+//
+// Notation follows the paper (arXiv 2106.15214): V (F x N), W (F x K),
+// H (K x N), Vt = Wt Ht the product at the current iterate, and the two
+// elementwise terms of eq. alt_update / eq. jnt_update:
+//     A = V . Vt^(beta-2)          B = Vt^(beta-1) = Vt . Vt^(beta-2)
+// B is formed as Vt times the same power so that V == Vt gives A == B.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nmf {
+
+// Compile-time specialisation of beta. The paper singles out beta = 0, 1, 2
+// (Table 2); beta = 1.5 is the hyperspectral case of Sec. 4.5.
+enum BetaKind : int { BK_GENERAL = 0, BK_IS = 1, BK_KL = 2, BK_EUC = 3, BK_B15 = 4 };
+
+inline int beta_kind(double beta) {
+  if (beta == 0.0) return BK_IS;
+  if (beta == 1.0) return BK_KL;
+  if (beta == 2.0) return BK_EUC;
+  if (beta == 1.5) return BK_B15;
+  return BK_GENERAL;
+}
+
+// gamma(beta), eq. def_gamma.
+inline double gamma_of(double beta) {
+  if (beta < 1.0) return 1.0 / (2.0 - beta);
+  if (beta <= 2.0) return 1.0;
+  return 1.0 / (beta - 1.0);
+}
+
+struct BetaParams {
+  double beta;
+  double gamma;
+  double kappa;
+  int kind;
+};
+
+// One problem of a (possibly batched) context. Every pointer is device memory.
+template <typename T>
+struct Prob {
+  const T* V;
+  int64_t ldv;
+  T* W;       // current W (in/out)
+  T* H;       // current H (in/out)
+  T* Wt;      // W at the start of the outer iteration (tilde point)
+  T* Ht;      // H at the start of the outer iteration
+  T* chiW1;   // chi_1(W, Wt), F x K
+  T* chiW2;   // chi_2(W, Wt), F x K
+  T* chiH1;   // chi_1(H, Ht), K x N
+  T* chiH2;   // chi_2(H, Ht), K x N
+  T* rowPart; // [S][2][F][K] partial numerators/denominators of the W half
+  T* colPart; // [R][2][K][N] partial numerators/denominators of the H half
+  T* norms;   // K column norms of W
+  int64_t F, N;
+  int K;
+  int S;             // column chunks of a row sweep
+  int R;             // row chunks of a column sweep
+  int rowTilesF;     // ceil(F / BF)
+  int colTilesN;     // ceil(N / BN)
+  int64_t chunkN;    // columns per row-sweep chunk (multiple of BN)
+  int64_t chunkF;    // rows per column-sweep chunk (multiple of BF)
+};
+
+// Finds the problem owning linear block index `b` given an exclusive prefix
+// table of block counts (prefix[count] = total).
+__device__ __forceinline__ int find_problem(const int* prefix, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise terms
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float pow_t(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double pow_t(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+
+// A = v . vt^(beta-2), B = vt . vt^(beta-2) (v and vt already include kappa).
+template <int BK, typename T>
+__device__ __forceinline__ void ab_terms(T v, T vt, T bm2, T& A, T& B) {
+  if (BK == BK_KL) {
+    A = v / vt;
+    B = T(1);
+  } else if (BK == BK_EUC) {
+    A = v;
+    B = vt;
+  } else if (BK == BK_IS) {
+    T r = T(1) / vt;
+    B = r;
+    A = v * r * r;
+  } else if (BK == BK_B15) {
+    T r = rsqrt_t(vt);
+    A = v * r;
+    B = vt * r;
+  } else {
+    T p = pow_t(vt, bm2);
+    A = v * p;
+    B = vt * p;
+  }
+}
+
+// (num / den)^gamma
+template <int BK, typename T>
+__device__ __forceinline__ T mu_ratio(T num, T den, T gamma) {
+  T r = num / den;
+  if (BK == BK_KL || BK == BK_EUC || BK == BK_B15) return r;  // gamma = 1 on [1, 2]
+  if (BK == BK_IS) return sqrt_t(r);                           // gamma = 1/2
+  return pow_t(r, gamma);
+}
+
+// chi_1(x, xt) and chi_2(x, xt) of eq. jnt_update, written with rho = x / xt:
+//   chi_1 = xt^(2-b) / x^(1-b) = xt rho^(b-1)   (b <= 2),   x   (b > 2)
+//   chi_2 = x                                    (b < 1),    x^b / xt^(b-1) = xt rho^b (b >= 1)
+template <int BK, typename T>
+__device__ __forceinline__ void chi_terms(T x, T xt, T beta, T& c1, T& c2) {
+  if (BK == BK_KL) { c1 = xt; c2 = x; return; }
+  if (BK == BK_EUC) { c1 = x; c2 = x * (x / xt); return; }
+  if (BK == BK_IS) { c1 = xt * (xt / x); c2 = x; return; }
+  T rho = x / xt;
+  if (BK == BK_B15) { c1 = xt * sqrt_t(rho); c2 = x * sqrt_t(rho); return; }
+  c1 = (beta <= T(2)) ? xt * pow_t(rho, beta - T(1)) : x;
+  c2 = (beta < T(1)) ? x : xt * pow_t(rho, beta);
+}
+
+// d_beta(x | y), eq. beta-div. Double: the formula as printed (0 log 0 = 0).
+__device__ __forceinline__ double dbeta_direct(double x, double y, double beta, int bk) {
+  if (bk == BK_KL) return (x > 0.0 ? x * log(x / y) : 0.0) - x + y;
+  if (bk == BK_IS) { double r = x / y; return r - log(r) - 1.0; }
+  if (bk == BK_EUC) { double d = x - y; return 0.5 * d * d; }
+  return pow(x, beta) / (beta * (beta - 1.0)) + pow(y, beta) / beta
+         - x * pow(y, beta - 1.0) / (beta - 1.0);
+}
+
+// Float: d = y^b phi_b(u) with u = x/y - 1 and
+// phi_b(u) = ((1+u)^b - 1 - b u) / (b (b-1)); near u = 0 the Taylor series
+// u^2/2 + (b-2)u^3/6 + (b-2)(b-3)u^4/24 + ... avoids the cancellation that
+// the printed formula suffers in single precision. beta = 1 and 0 are the
+// limits (1+u) log1p(u) - u and u - log1p(u).
+__device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int bk) {
+  if (bk == BK_EUC) { float d = x - y; return 0.5f * d * d; }
+  if (bk == BK_KL && x <= 0.0f) return y;
+  float u = (x - y) / y;
+  float phi;
+  if (fabsf(u) < 0.1f) {
+    float c = 0.5f, s = 0.0f, up = u * u;
+    #pragma unroll
+    for (int j = 2; j <= 8; ++j) {   // coefficient of u^j: prod_{i=2}^{j-1} (b - i) / j!
+      s += c * up;
+      up *= u;
+      c *= (beta - float(j)) / float(j + 1);
+    }
+    phi = s;
+  } else if (bk == BK_KL) {
+    phi = (1.0f + u) * log1pf(u) - u;
+  } else if (bk == BK_IS) {
+    phi = u - log1pf(u);
+  } else {
+    phi = (expm1f(beta * log1pf(u)) - beta * u) / (beta * (beta - 1.0f));
+  }
+  float yb = (bk == BK_KL) ? y : (bk == BK_IS ? 1.0f : powf(y, beta));
+  return yb * phi;
+}
+
+template <typename T> struct DB;
+template <> struct DB<double> {
+  __device__ static double eval(double x, double y, double beta, int bk) { return dbeta_direct(x, y, beta, bk); }
+};
+template <> struct DB<float> {
+  __device__ static double eval(float x, float y, double beta, int bk) {
+    return (double)dbeta_stable(x, y, (float)beta, bk);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum (any blockDim multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = (l < nw) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+}  // namespace nmf

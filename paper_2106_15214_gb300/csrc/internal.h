@@ -1,0 +1,162 @@
+// internal.h -- host-side declarations shared by the translation units of libnmf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace nmf {
+
+constexpr int BF = 32;     // rows per SIMT tile
+constexpr int BN = 32;     // columns per SIMT tile
+constexpr int NT = 256;    // threads per SIMT block
+constexpr int EW = 256;    // entries per elementwise block
+constexpr int KMAX = 128;  // largest rank the SIMT kernels accept
+
+// Per-context launch counting and optional CUDA-event timing of each kernel
+// (nmf_set_timing / nmf_get_timing). Event pairs are resolved lazily.
+struct Timer {
+  struct Rec { const char* name; int64_t launches; double ms; };
+  struct Pending { cudaEvent_t a, b; int rec; };
+  bool on = false;
+  int64_t total = 0;
+  std::vector<Rec> recs;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+
+  int rec_index(const char* name) {
+    for (size_t i = 0; i < recs.size(); ++i)
+      if (recs[i].name == name) return (int)i;
+    recs.push_back({name, 0, 0.0});
+    return (int)recs.size() - 1;
+  }
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+  }
+  // Adds the elapsed time of every recorded pair (the stream must be synchronised).
+  void resolve() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) recs[p.rec].ms += ms;
+      else cudaGetLastError();
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() { resolve(); recs.clear(); total = 0; }
+  ~Timer() {
+    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Runs a launcher (which issues `nkern` kernels) under the timer.
+template <typename Fn>
+inline cudaError_t timed(Timer* t, cudaStream_t st, const char* name, int nkern, Fn&& fn) {
+  if (!t) return fn();
+  const int r = t->rec_index(name);
+  t->recs[r].launches += nkern;
+  t->total += nkern;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t->on) {
+    a = t->get();
+    b = t->get();
+    if (a && b) cudaEventRecord(a, st);
+  }
+  cudaError_t e = fn();
+  if (t->on && a && b) {
+    cudaEventRecord(b, st);
+    t->pending.push_back({a, b, r});
+  }
+  return e;
+}
+
+// Operand selectors of the sweeps (see sweeps_impl.cuh).
+enum { SEL_CUR = 0, SEL_TILDE = 1 };      // W or Wt, H or Ht
+enum { OP_SELF = 0, OP_CHI = 1 };         // D1 = D2 = Hp (C1 = C2 = Wp) or the chi buffers
+enum { SWEEP_CONTRACT = 1, SWEEP_LOSS = 2 };
+enum { EPI_UPDATE = 0, EPI_GRAD = 1 };
+
+// Device tables of a context for element type T.
+template <typename T>
+struct Plan {
+  Prob<T>* d_probs = nullptr;
+  int count = 0;
+  int maxK = 0;
+  int* d_prefRow = nullptr; int totRow = 0;   // row-sweep blocks per problem
+  int* d_prefCol = nullptr; int totCol = 0;   // column-sweep blocks
+  int* d_prefW = nullptr; int totW = 0;       // EW-entry blocks over F x K
+  int* d_prefH = nullptr; int totH = 0;       // EW-entry blocks over K x N
+  int* d_prefK = nullptr; int totK = 0;       // one block per column of W
+};
+
+template <typename T>
+cudaError_t launch_row_sweep(const Plan<T>& pl, int wsel, int hsel, int dsel, int flags,
+                             const BetaParams& bp, double* lossPart, const int* status,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, int flags,
+                             const BetaParams& bp, double* lossPart, const int* status,
+                             cudaStream_t st);
+// W epilogue: W = base . (sum num / sum den)^gamma (mode EPI_UPDATE, base = W or Wt,
+// chi computed from (W_new, Wt) when want_chi) or gout = sum den - sum num (EPI_GRAD).
+template <typename T>
+cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st);
+// Copies W -> Wt and H -> Ht for every problem (skipped once status is set).
+template <typename T>
+cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st);
+// Column l2 norms of W, then W[:,k] /= n_k, H[k,:] *= n_k (zero norms untouched).
+template <typename T>
+cudaError_t launch_normalize(const Plan<T>& pl, const int* status, cudaStream_t st);
+// out[i] = fixed-order sum of lossPart over problem i's blocks of the given prefix table.
+cudaError_t launch_loss_finalize(const int* d_prefix, int count, const double* lossPart,
+                                 double* out, cudaStream_t st);
+// KKT residual sums: out[0] = sum |min(W, gW)|, out[1] = sum |min(H, gH)| (single problem).
+template <typename T>
+cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T* gH,
+                       int64_t nH, double* out, cudaStream_t st);
+
+// Sparse beta = 1 path (sparse_kl.cu).
+struct SparseKL {
+  int64_t F = 0, N = 0, nnz = 0;
+  int K = 0;
+  const int32_t* rowptr = nullptr;  // CSR (borrowed)
+  const int32_t* col = nullptr;
+  const float* val = nullptr;
+  int32_t* rowidx = nullptr;        // row of each CSR entry (owned)
+  int32_t* colptr = nullptr;        // CSC (owned)
+  int32_t* cscRow = nullptr;
+  int64_t* cscPos = nullptr;        // CSC entry -> CSR position
+  float* a = nullptr;               // A = V / Vt at the nonzeros, CSR order
+  float* Wt = nullptr;
+  float* Ht = nullptr;
+  float* colsumW = nullptr;         // K
+  float* rowsumH = nullptr;         // K
+  float* chi = nullptr;             // scratch K-vector
+  double* lossPart = nullptr;
+  int lossBlocks = 0;
+  double* sums = nullptr;           // scratch doubles
+};
+cudaError_t sparse_build_csc(SparseKL& s, void* tmp, size_t tmpBytes, cudaStream_t st);
+size_t sparse_csc_tmp_bytes(int64_t F, int64_t N, int64_t nnz);
+cudaError_t sparse_step(SparseKL& s, float* W, float* H, bool joint, bool hfirst,
+                        bool wantLoss, bool normalize, int* status, Timer* tm, cudaStream_t st);
+cudaError_t sparse_loss_finalize(SparseKL& s, const float* W, const float* H, double* out,
+                                 cudaStream_t st);
+cudaError_t sparse_loss(SparseKL& s, const float* W, const float* H, double* out,
+                        cudaStream_t st);
+cudaError_t sparse_grad(SparseKL& s, const float* W, const float* H, float* gW, float* gH,
+                        cudaStream_t st);
+
+}  // namespace nmf

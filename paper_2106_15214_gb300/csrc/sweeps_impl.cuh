@@ -1,0 +1,541 @@
+// sweeps_impl.cuh -- SIMT kernels of the dense path, templated on the element
+// type (double for NMF_FP64, float for NMF_FP32).
+//
+// Every update of Algorithm 1 (BMM, eq. alt_update) and Algorithm 2 (JMM,
+// eq. jnt_update) is a product of the two elementwise terms
+//     A = (V + kappa) . Vp^(beta-2),   B = Vp . Vp^(beta-2),   Vp = Wp Hp + kappa
+// with a factor-shaped matrix, reduced either over columns n (the W half) or
+// over rows f (the H half):
+//   row sweep:    P = A D1^T,  Q = B D2^T     (F x K, reduced over n)
+//   column sweep: Hn = C1^T A, Hd = C2^T B    (K x N, reduced over f)
+// JMM takes Wp = Wt, Hp = Ht (the product is formed at the iterate only,
+// Algorithm 2) and D/C = chi_1, chi_2 of the other factor; BMM takes the
+// current factors and D = C = that factor. Vp is recomputed per tile in
+// shared memory and never stored.
+//
+// Tiling: a block owns a BF x BN tile at a time; phase A forms Vp, A and B
+// for the tile in shared memory (plus the objective when asked, eq.
+// obj_fct), phase B accumulates the contraction in registers. Partial sums go
+// to per-chunk slices that the epilogue adds in a fixed order, so every
+// result is deterministic.
+#pragma once
+
+#include "internal.h"
+
+namespace nmf {
+
+constexpr int TP = BN + 1;  // padded shared-memory row of a BN-wide tile
+
+__device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Phase A: Vp, A, B for rows [f0, f0+BF) x cols [n0, n0+BN) of one problem.
+// Ws: [BF][KP] rows of Wp; Hs: [K][TP] columns of Hp. Out-of-range entries get
+// A = B = 0 so they add nothing. Returns this thread's share of the objective.
+template <typename T, int BK>
+__device__ __forceinline__ T phase_a(const T* Ws, int KP, const T* Hs, int K,
+                                     const T* __restrict__ V, int64_t ldv, int64_t f0,
+                                     int64_t fLim, int64_t n0, int64_t nLim,
+                                     const BetaParams& bp, T* As, T* Bs, bool wantLoss) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T kappa = (T)bp.kappa, bm2 = (T)(bp.beta - 2.0);
+  T tl = T(0);
+  #pragma unroll
+  for (int i = 0; i < BF / 8; ++i) {
+    const int f = warp + 8 * i;
+    const int64_t gf = f0 + f, gn = n0 + lane;
+    T a = T(0), b = T(0);
+    if (gf < fLim && gn < nLim) {
+      T vt = T(0);
+      const T* wrow = Ws + f * KP;
+      for (int k = 0; k < K; ++k) vt = fma(wrow[k], Hs[k * TP + lane], vt);
+      vt += kappa;
+      const T v = V[gf * ldv + gn] + kappa;
+      ab_terms<BK, T>(v, vt, bm2, a, b);
+      if (wantLoss) tl += (T)DB<T>::eval(v, vt, bp.beta, BK);
+    }
+    As[f * TP + lane] = a;
+    Bs[f * TP + lane] = b;
+  }
+  return tl;
+}
+
+template <typename T, int BK, int KJ>
+__global__ void __launch_bounds__(NT)
+row_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
+                 int wsel, int hsel, int dsel, int flags, BetaParams bp,
+                 double* __restrict__ lossPart, const int* __restrict__ status) {
+  if (*status) return;
+  const int b = blockIdx.x;
+  const int pi = find_problem(prefix, count, b);
+  const Prob<T> P = probs[pi];
+  const int local = b - prefix[pi];
+  const int ft = local % P.rowTilesF;
+  const int s = local / P.rowTilesF;
+  const int K = P.K, KP = K + 1;
+  const bool contract = flags & SWEEP_CONTRACT, wantLoss = flags & SWEEP_LOSS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);
+  T* Hs = Ws + BF * KP;
+  T* D1s = Hs + K * TP;
+  T* D2s = D1s + K * TP;
+  T* As = dsel == OP_CHI ? D2s + K * TP : D1s;
+  T* Bs = As + BF * TP;
+  __shared__ double red[32];
+
+  const T* __restrict__ Wp = wsel == SEL_TILDE ? P.Wt : P.W;
+  const T* __restrict__ Hp = hsel == SEL_TILDE ? P.Ht : P.H;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t f0 = (int64_t)ft * BF;
+  for (int i = tid; i < BF * K; i += NT) {
+    const int f = i / K, k = i - f * K;
+    Ws[f * KP + k] = (f0 + f < P.F) ? Wp[(f0 + f) * K + k] : T(0);
+  }
+  T accP[BF / 8][KJ], accQ[BF / 8][KJ];
+  #pragma unroll
+  for (int i = 0; i < BF / 8; ++i)
+    #pragma unroll
+    for (int j = 0; j < KJ; ++j) accP[i][j] = accQ[i][j] = T(0);
+  double loss = 0.0;
+  const int64_t nBeg = (int64_t)s * P.chunkN;
+  const int64_t nEnd = lmin(P.N, nBeg + P.chunkN);
+  for (int64_t n0 = nBeg; n0 < nEnd; n0 += BN) {
+    __syncthreads();
+    for (int i = tid; i < K * BN; i += NT) {
+      const int k = i / BN, n = i - k * BN;
+      const int64_t gn = n0 + n;
+      const bool in = gn < nEnd;
+      Hs[k * TP + n] = in ? Hp[k * P.N + gn] : T(0);
+      if (dsel == OP_CHI) {
+        D1s[k * TP + n] = in ? P.chiH1[k * P.N + gn] : T(0);
+        D2s[k * TP + n] = in ? P.chiH2[k * P.N + gn] : T(0);
+      }
+    }
+    __syncthreads();
+    T tl = phase_a<T, BK>(Ws, KP, Hs, K, P.V, P.ldv, f0, P.F, n0, nEnd, bp, As, Bs, wantLoss);
+    if (wantLoss) loss += (double)tl;
+    if (!contract) continue;
+    __syncthreads();
+    const T* D1 = dsel == OP_CHI ? D1s : Hs;
+    const T* D2 = dsel == OP_CHI ? D2s : Hs;
+    #pragma unroll 4
+    for (int n = 0; n < BN; ++n) {
+      T av[BF / 8], bv[BF / 8];
+      #pragma unroll
+      for (int i = 0; i < BF / 8; ++i) {
+        av[i] = As[(warp + 8 * i) * TP + n];
+        bv[i] = Bs[(warp + 8 * i) * TP + n];
+      }
+      #pragma unroll
+      for (int j = 0; j < KJ; ++j) {
+        const int k = lane + 32 * j;
+        const T d1 = k < K ? D1[k * TP + n] : T(0);
+        const T d2 = k < K ? D2[k * TP + n] : T(0);
+        #pragma unroll
+        for (int i = 0; i < BF / 8; ++i) {
+          accP[i][j] = fma(av[i], d1, accP[i][j]);
+          accQ[i][j] = fma(bv[i], d2, accQ[i][j]);
+        }
+      }
+    }
+  }
+  if (contract) {
+    T* part = P.rowPart + (int64_t)s * 2 * P.F * K;
+    #pragma unroll
+    for (int i = 0; i < BF / 8; ++i) {
+      const int64_t gf = f0 + warp + 8 * i;
+      #pragma unroll
+      for (int j = 0; j < KJ; ++j) {
+        const int k = lane + 32 * j;
+        if (gf < P.F && k < K) {
+          part[gf * K + k] = accP[i][j];
+          part[P.F * K + gf * K + k] = accQ[i][j];
+        }
+      }
+    }
+  }
+  if (wantLoss) {
+    const double t = block_sum(loss, red);
+    if (tid == 0) lossPart[b] = t;
+  }
+}
+
+template <typename T, int BK, int KJ8>
+__global__ void __launch_bounds__(NT)
+col_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
+                 int wsel, int hsel, int csel, int flags, BetaParams bp,
+                 double* __restrict__ lossPart, const int* __restrict__ status) {
+  if (*status) return;
+  const int b = blockIdx.x;
+  const int pi = find_problem(prefix, count, b);
+  const Prob<T> P = probs[pi];
+  const int local = b - prefix[pi];
+  const int nt = local % P.colTilesN;
+  const int r = local / P.colTilesN;
+  const int K = P.K, KP = K + 1;
+  const bool contract = flags & SWEEP_CONTRACT, wantLoss = flags & SWEEP_LOSS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Hs = reinterpret_cast<T*>(smem_raw);
+  T* Ws = Hs + K * TP;
+  T* C1s = Ws + BF * KP;
+  T* C2s = C1s + BF * KP;
+  T* As = csel == OP_CHI ? C2s + BF * KP : C1s;
+  T* Bs = As + BF * TP;
+  __shared__ double red[32];
+
+  const T* __restrict__ Wp = wsel == SEL_TILDE ? P.Wt : P.W;
+  const T* __restrict__ Hp = hsel == SEL_TILDE ? P.Ht : P.H;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n0 = (int64_t)nt * BN;
+  for (int i = tid; i < K * BN; i += NT) {
+    const int k = i / BN, n = i - k * BN;
+    Hs[k * TP + n] = (n0 + n < P.N) ? Hp[k * P.N + n0 + n] : T(0);
+  }
+  T num[KJ8], den[KJ8];
+  #pragma unroll
+  for (int j = 0; j < KJ8; ++j) num[j] = den[j] = T(0);
+  double loss = 0.0;
+  const int64_t fBeg = (int64_t)r * P.chunkF;
+  const int64_t fEnd = lmin(P.F, fBeg + P.chunkF);
+  for (int64_t f0 = fBeg; f0 < fEnd; f0 += BF) {
+    __syncthreads();
+    for (int i = tid; i < BF * K; i += NT) {
+      const int f = i / K, k = i - f * K;
+      const int64_t gf = f0 + f;
+      const bool in = gf < fEnd;
+      Ws[f * KP + k] = in ? Wp[gf * K + k] : T(0);
+      if (csel == OP_CHI) {
+        C1s[f * KP + k] = in ? P.chiW1[gf * K + k] : T(0);
+        C2s[f * KP + k] = in ? P.chiW2[gf * K + k] : T(0);
+      }
+    }
+    __syncthreads();
+    T tl = phase_a<T, BK>(Ws, KP, Hs, K, P.V, P.ldv, f0, fEnd, n0, P.N, bp, As, Bs, wantLoss);
+    if (wantLoss) loss += (double)tl;
+    if (!contract) continue;
+    __syncthreads();
+    const T* C1 = csel == OP_CHI ? C1s : Ws;
+    const T* C2 = csel == OP_CHI ? C2s : Ws;
+    #pragma unroll 4
+    for (int f = 0; f < BF; ++f) {
+      const T a = As[f * TP + lane], bb = Bs[f * TP + lane];
+      #pragma unroll
+      for (int j = 0; j < KJ8; ++j) {
+        const int k = warp + 8 * j;
+        if (k < K) {
+          num[j] = fma(C1[f * KP + k], a, num[j]);
+          den[j] = fma(C2[f * KP + k], bb, den[j]);
+        }
+      }
+    }
+  }
+  if (contract) {
+    T* part = P.colPart + (int64_t)r * 2 * K * P.N;
+    const int64_t gn = n0 + lane;
+    #pragma unroll
+    for (int j = 0; j < KJ8; ++j) {
+      const int k = warp + 8 * j;
+      if (k < K && gn < P.N) {
+        part[k * P.N + gn] = num[j];
+        part[(int64_t)K * P.N + k * P.N + gn] = den[j];
+      }
+    }
+  }
+  if (wantLoss) {
+    const double t = block_sum(loss, red);
+    if (tid == 0) lossPart[b] = t;
+  }
+}
+
+// W-half epilogue over F x K entries.
+template <typename T, int BK>
+__global__ void __launch_bounds__(EW)
+rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
+                     int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
+                     int* __restrict__ status) {
+  if (*status) return;
+  const int b = blockIdx.x;
+  const int pi = find_problem(prefix, count, b);
+  const Prob<T> P = probs[pi];
+  const int64_t FK = P.F * P.K;
+  const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
+  if (idx >= FK) return;
+  T num = T(0), den = T(0);
+  for (int s = 0; s < P.S; ++s) {
+    num += P.rowPart[(int64_t)s * 2 * FK + idx];
+    den += P.rowPart[(int64_t)s * 2 * FK + FK + idx];
+  }
+  if (mode == EPI_GRAD) { gout[idx] = den - num; return; }
+  const T base = basesel == SEL_TILDE ? P.Wt[idx] : P.W[idx];
+  const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+  if (!isfinite(x)) atomicExch(status, 4);
+  P.W[idx] = x;
+  if (want_chi) {
+    T c1, c2;
+    chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
+    P.chiW1[idx] = c1;
+    P.chiW2[idx] = c2;
+  }
+}
+
+// H-half epilogue over K x N entries.
+template <typename T, int BK>
+__global__ void __launch_bounds__(EW)
+cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
+                     int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
+                     int* __restrict__ status) {
+  if (*status) return;
+  const int b = blockIdx.x;
+  const int pi = find_problem(prefix, count, b);
+  const Prob<T> P = probs[pi];
+  const int64_t KN = (int64_t)P.K * P.N;
+  const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
+  if (idx >= KN) return;
+  T num = T(0), den = T(0);
+  for (int r = 0; r < P.R; ++r) {
+    num += P.colPart[(int64_t)r * 2 * KN + idx];
+    den += P.colPart[(int64_t)r * 2 * KN + KN + idx];
+  }
+  if (mode == EPI_GRAD) { gout[idx] = den - num; return; }
+  const T base = basesel == SEL_TILDE ? P.Ht[idx] : P.H[idx];
+  const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+  if (!isfinite(x)) atomicExch(status, 4);
+  P.H[idx] = x;
+  if (want_chi) {
+    T c1, c2;
+    chi_terms<BK, T>(x, P.Ht[idx], (T)bp.beta, c1, c2);
+    P.chiH1[idx] = c1;
+    P.chiH2[idx] = c2;
+  }
+}
+
+// Blocks [0, totW) copy W -> Wt, blocks [totW, totW + totH) copy H -> Ht.
+template <typename T>
+__global__ void __launch_bounds__(EW)
+begin_iteration_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefW,
+                       int totW, const int* __restrict__ prefH, const int* __restrict__ status) {
+  if (*status) return;
+  int b = blockIdx.x;
+  if (b < totW) {
+    const int pi = find_problem(prefW, count, b);
+    const Prob<T> P = probs[pi];
+    const int64_t idx = (int64_t)(b - prefW[pi]) * EW + threadIdx.x;
+    if (idx < P.F * P.K) P.Wt[idx] = P.W[idx];
+  } else {
+    b -= totW;
+    const int pi = find_problem(prefH, count, b);
+    const Prob<T> P = probs[pi];
+    const int64_t idx = (int64_t)(b - prefH[pi]) * EW + threadIdx.x;
+    if (idx < (int64_t)P.K * P.N) P.Ht[idx] = P.H[idx];
+  }
+}
+
+// One block per column k of W: norms[k] = ||W[:, k]||_2 (fixed-order sum).
+template <typename T>
+__global__ void __launch_bounds__(EW)
+colnorm_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefK,
+               const int* __restrict__ status) {
+  if (*status) return;
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const int pi = find_problem(prefK, count, b);
+  const Prob<T> P = probs[pi];
+  const int k = b - prefK[pi];
+  double s = 0.0;
+  for (int64_t f = threadIdx.x; f < P.F; f += EW) {
+    const double w = (double)P.W[f * P.K + k];
+    s += w * w;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) P.norms[k] = (T)sqrt(s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EW)
+normalize_apply_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefW,
+                       int totW, const int* __restrict__ prefH, const int* __restrict__ status) {
+  if (*status) return;
+  int b = blockIdx.x;
+  if (b < totW) {
+    const int pi = find_problem(prefW, count, b);
+    const Prob<T> P = probs[pi];
+    const int64_t idx = (int64_t)(b - prefW[pi]) * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const T nk = P.norms[idx % P.K];
+      if (nk > T(0)) P.W[idx] = P.W[idx] / nk;
+    }
+  } else {
+    b -= totW;
+    const int pi = find_problem(prefH, count, b);
+    const Prob<T> P = probs[pi];
+    const int64_t idx = (int64_t)(b - prefH[pi]) * EW + threadIdx.x;
+    if (idx < (int64_t)P.K * P.N) {
+      const T nk = P.norms[idx / P.N];
+      if (nk > T(0)) P.H[idx] = P.H[idx] * nk;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EW)
+kkt_kernel(const T* __restrict__ W, const T* __restrict__ gW, int64_t nW, const T* __restrict__ H,
+           const T* __restrict__ gH, int64_t nH, double* __restrict__ out) {
+  __shared__ double red[32];
+  double sw = 0.0, sh = 0.0;
+  for (int64_t i = threadIdx.x; i < nW; i += EW) sw += fabs((double)min(W[i], gW[i]));
+  for (int64_t i = threadIdx.x; i < nH; i += EW) sh += fabs((double)min(H[i], gH[i]));
+  sw = block_sum(sw, red);
+  __syncthreads();
+  sh = block_sum(sh, red);
+  if (threadIdx.x == 0) { out[0] = sw; out[1] = sh; }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+inline size_t row_smem_bytes(int K, int dsel) {
+  return sizeof(T) * ((size_t)BF * (K + 1) + (size_t)K * TP * (dsel == OP_CHI ? 3 : 1) + 2 * BF * TP);
+}
+template <typename T>
+inline size_t col_smem_bytes(int K, int csel) {
+  return sizeof(T) * ((size_t)K * TP + (size_t)BF * (K + 1) * (csel == OP_CHI ? 3 : 1) + 2 * BF * TP);
+}
+
+template <typename KernelT>
+inline cudaError_t prep_smem(KernelT kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int BK, int KJ>
+cudaError_t row_sweep_bk_kj(const Plan<T>& pl, int wsel, int hsel, int dsel, int flags,
+                            const BetaParams& bp, double* lossPart, const int* status,
+                            cudaStream_t st) {
+  auto kern = row_sweep_kernel<T, BK, KJ>;
+  const size_t sm = row_smem_bytes<T>(pl.maxK, dsel);
+  cudaError_t e = prep_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  kern<<<pl.totRow, NT, sm, st>>>(pl.d_probs, pl.count, pl.d_prefRow, wsel, hsel, dsel, flags, bp,
+                                  lossPart, status);
+  return cudaGetLastError();
+}
+
+template <typename T, int BK>
+cudaError_t row_sweep_bk(const Plan<T>& pl, int wsel, int hsel, int dsel, int flags,
+                         const BetaParams& bp, double* lossPart, const int* status, cudaStream_t st) {
+  if (pl.maxK <= 32) return row_sweep_bk_kj<T, BK, 1>(pl, wsel, hsel, dsel, flags, bp, lossPart, status, st);
+  if (pl.maxK <= 64) return row_sweep_bk_kj<T, BK, 2>(pl, wsel, hsel, dsel, flags, bp, lossPart, status, st);
+  return row_sweep_bk_kj<T, BK, 4>(pl, wsel, hsel, dsel, flags, bp, lossPart, status, st);
+}
+
+template <typename T, int BK, int KJ8>
+cudaError_t col_sweep_bk_kj(const Plan<T>& pl, int wsel, int hsel, int csel, int flags,
+                            const BetaParams& bp, double* lossPart, const int* status,
+                            cudaStream_t st) {
+  auto kern = col_sweep_kernel<T, BK, KJ8>;
+  const size_t sm = col_smem_bytes<T>(pl.maxK, csel);
+  cudaError_t e = prep_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  kern<<<pl.totCol, NT, sm, st>>>(pl.d_probs, pl.count, pl.d_prefCol, wsel, hsel, csel, flags, bp,
+                                  lossPart, status);
+  return cudaGetLastError();
+}
+
+template <typename T, int BK>
+cudaError_t col_sweep_bk(const Plan<T>& pl, int wsel, int hsel, int csel, int flags,
+                         const BetaParams& bp, double* lossPart, const int* status, cudaStream_t st) {
+  if (pl.maxK <= 16) return col_sweep_bk_kj<T, BK, 2>(pl, wsel, hsel, csel, flags, bp, lossPart, status, st);
+  if (pl.maxK <= 32) return col_sweep_bk_kj<T, BK, 4>(pl, wsel, hsel, csel, flags, bp, lossPart, status, st);
+  if (pl.maxK <= 64) return col_sweep_bk_kj<T, BK, 8>(pl, wsel, hsel, csel, flags, bp, lossPart, status, st);
+  return col_sweep_bk_kj<T, BK, 16>(pl, wsel, hsel, csel, flags, bp, lossPart, status, st);
+}
+
+#define NMF_BK_DISPATCH(FN, ...)                                   \
+  switch (bp.kind) {                                               \
+    case BK_IS: return FN<T, BK_IS>(__VA_ARGS__);                  \
+    case BK_KL: return FN<T, BK_KL>(__VA_ARGS__);                  \
+    case BK_EUC: return FN<T, BK_EUC>(__VA_ARGS__);                \
+    case BK_B15: return FN<T, BK_B15>(__VA_ARGS__);                \
+    default: return FN<T, BK_GENERAL>(__VA_ARGS__);                \
+  }
+
+template <typename T>
+cudaError_t launch_row_sweep(const Plan<T>& pl, int wsel, int hsel, int dsel, int flags,
+                             const BetaParams& bp, double* lossPart, const int* status,
+                             cudaStream_t st) {
+  NMF_BK_DISPATCH(row_sweep_bk, pl, wsel, hsel, dsel, flags, bp, lossPart, status, st)
+}
+
+template <typename T>
+cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, int flags,
+                             const BetaParams& bp, double* lossPart, const int* status,
+                             cudaStream_t st) {
+  NMF_BK_DISPATCH(col_sweep_bk, pl, wsel, hsel, csel, flags, bp, lossPart, status, st)
+}
+
+template <typename T, int BK>
+cudaError_t rows_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+  rows_epilogue_kernel<T, BK><<<pl.totW, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, mode,
+                                                      basesel, want_chi, bp, gout, status);
+  return cudaGetLastError();
+}
+template <typename T, int BK>
+cudaError_t cols_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+  cols_epilogue_kernel<T, BK><<<pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefH, mode,
+                                                      basesel, want_chi, bp, gout, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+  NMF_BK_DISPATCH(rows_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st)
+}
+template <typename T>
+cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+  NMF_BK_DISPATCH(cols_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st)
+}
+
+template <typename T>
+cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st) {
+  begin_iteration_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
+                                                               pl.totW, pl.d_prefH, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_normalize(const Plan<T>& pl, const int* status, cudaStream_t st) {
+  colnorm_kernel<T><<<pl.totK, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefK, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  normalize_apply_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
+                                                               pl.totW, pl.d_prefH, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T* gH, int64_t nH,
+                       double* out, cudaStream_t st) {
+  kkt_kernel<T><<<1, EW, 0, st>>>(W, gW, nW, H, gH, nH, out);
+  return cudaGetLastError();
+}
+
+#define NMF_INSTANTIATE_SWEEPS(T)                                                                   \
+  template cudaError_t launch_row_sweep<T>(const Plan<T>&, int, int, int, int, const BetaParams&,  \
+                                           double*, const int*, cudaStream_t);                     \
+  template cudaError_t launch_col_sweep<T>(const Plan<T>&, int, int, int, int, const BetaParams&,  \
+                                           double*, const int*, cudaStream_t);                     \
+  template cudaError_t launch_rows_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
+                                               T*, int*, cudaStream_t);                            \
+  template cudaError_t launch_cols_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
+                                               T*, int*, cudaStream_t);                            \
+  template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
+  template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
+  template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \
+                                     double*, cudaStream_t);
+
+}  // namespace nmf
