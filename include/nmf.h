@@ -181,6 +181,36 @@ nmf_status nmf_get_timing(nmf_ctx* ctx, int32_t i, const char** name, int64_t* l
 /* Clears the timing records and launch counts. */
 nmf_status nmf_reset_timing(nmf_ctx* ctx);
 
+/* Objective without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * running while a CUDA stream capture is active, hosts that give the library a
+ * fixed memory budget or forbid driver allocations, and latency-critical
+ * loops that cannot take cudaMalloc's implicit synchronisation. It computes
+ * the same value as nmf_loss, D_beta(V + kappa | WH + kappa) accumulated in
+ * FP64, without a context.
+ *
+ * Arguments: sizes, beta, kappa and precision as for nmf_create and
+ * nmf_set_options (NMF_FP64 means double buffers, every other precision
+ * float). V_dev (F x N, leading dimension ldv >= N), W_dev (F x K) and H_dev
+ * (K x N) are caller-owned device inputs, row-major; loss_dev is a
+ * caller-owned device double that receives the result. The call is
+ * asynchronous on cuda_stream (NULL: legacy default stream): read *loss_dev
+ * after synchronising that stream. It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Scratch: a static device array of 512 KB (65536 per-tile partial sums and a
+ * counter) that every GPU loading the library holds until the process exits.
+ * Limit: ceil(F/32) * ceil(N/32) <= 65536 (for example 8192 x 8192), else
+ * NMF_EINVAL and nothing is launched. All calls share the array; calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race on it,
+ * so serialise them. The first call on each device looks up the array's
+ * device address (once per device, with that device current); make that
+ * first call before any stream capture begins. */
+nmf_status nmf_loss_noalloc(int64_t F, int64_t N, int32_t K, double beta, double kappa,
+                            nmf_precision precision, const void* V_dev, int64_t ldv,
+                            const void* W_dev, const void* H_dev, double* loss_dev,
+                            void* cuda_stream);
+
 /* Frees the context and its scratch (not the borrowed buffers). NULL is a no-op. */
 void nmf_destroy(nmf_ctx* ctx);
 

@@ -23,7 +23,7 @@ EXPORTS = [
     "nmf_set_csr", "nmf_set_factors", "nmf_batch_set_packed", "nmf_step_joint",
     "nmf_step_alternating", "nmf_loss", "nmf_grad", "nmf_kkt", "nmf_batch_get_losses",
     "nmf_get_status", "nmf_step_joint_host", "nmf_set_timing", "nmf_get_timing", "nmf_reset_timing",
-    "nmf_destroy", "nmf_status_string",
+    "nmf_loss_noalloc", "nmf_destroy", "nmf_status_string",
 ]
 
 _lib = None
@@ -64,6 +64,7 @@ def _declare(lib):
         "nmf_set_timing": [P, ctypes.c_int],
         "nmf_get_timing": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64), PD],
         "nmf_reset_timing": [P],
+        "nmf_loss_noalloc": [I64, I64, I32, D, D, ctypes.c_int, P, I64, P, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -106,6 +107,25 @@ def _stream():
 def _dtype_for(precision):
     import torch
     return torch.float64 if precision == FP64 else torch.float32
+
+
+def loss_noalloc(V, W, H, beta, kappa=0.0, out=None, stream=None):
+    """nmf_loss_noalloc: the objective into a device double, with no device
+    allocation inside the library (for callers that cannot call cudaMalloc).
+    V, W, H are CUDA tensors (float64 or float32, row-major); `out` is a
+    one-element float64 CUDA tensor (allocated here by torch if not given).
+    Asynchronous on the stream; returns `out`."""
+    import torch
+    lib = load()
+    F, N = V.shape
+    K = W.shape[1]
+    prec = FP64 if V.dtype == torch.float64 else FP32
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=V.device)
+    s = ctypes.c_void_p(stream) if stream is not None else _stream()
+    check(lib.nmf_loss_noalloc(F, N, K, float(beta), float(kappa), prec, _ptr(V), V.stride(0), _ptr(W),
+                               _ptr(H), _ptr(out), s), "nmf_loss_noalloc")
+    return out
 
 
 class NMF:
