@@ -7,11 +7,11 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
 #include "nmf.h"
-#include "tc_dense.h"
 
 using namespace nmf;
 
@@ -68,7 +68,6 @@ struct nmf_ctx {
   void* stageV = nullptr;
   void* stageW = nullptr;
   void* stageH = nullptr;
-  TcState* tc = nullptr;
   SparseKL sp;
   Timer timer;
   int sms = 148;
@@ -92,8 +91,6 @@ void free_all(nmf_ctx* c) {
   c->allocs.clear();
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   c->h_pinned = nullptr;
-  if (c->tc) tc_destroy(c->tc);
-  c->tc = nullptr;
   c->prepared = false;
   c->tableDirty = true;
   c->cscBuilt = false;
@@ -150,6 +147,23 @@ bool data_ready(const nmf_ctx* c) {
   return c->V && c->W && c->H;
 }
 
+// Tensor-core sweeps: 128-row (row sweep) or 128-column (column sweep) MMA
+// tiles, split along the other dimension into chunks of 32-wide tiles until
+// about one block per SM.
+void tc_tiling(Prob<float>& P, int sms) {
+  const int64_t target = sms;
+  const int64_t nT = cdiv(P.N, 32), fT = cdiv(P.F, 32);
+  P.tcRowTiles = (int)cdiv(P.F, 128);
+  int64_t S = std::min<int64_t>(std::max<int64_t>(1, cdiv(target, P.tcRowTiles)), nT);
+  P.tcChunkN = cdiv(nT, S) * 32;
+  P.tcS = (int)cdiv(P.N, P.tcChunkN);
+  P.tcColTiles = (int)cdiv(P.N, 128);
+  int64_t R = std::min<int64_t>(std::max<int64_t>(1, cdiv(target, P.tcColTiles)), fT);
+  P.tcChunkF = cdiv(fT, R) * 32;
+  P.tcR = (int)cdiv(P.F, P.tcChunkF);
+}
+template <typename T> void tc_tiling(Prob<T>&, int) {}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename T>
@@ -167,12 +181,16 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     const int K = c->K[i];
     maxK = std::max(maxK, K);
     tl[i] = tiling(F, N, c->sms, c->batched);
+    probs[i].F = F; probs[i].N = N; probs[i].K = K;
+    probs[i].tcS = probs[i].tcR = 1;
+    if (!c->batched) tc_tiling(probs[i], c->sms);
+    const int Smax = std::max(tl[i].S, probs[i].tcS), Rmax = std::max(tl[i].R, probs[i].tcR);
     const size_t FK = (size_t)F * K, KN = (size_t)K * N;
     size_t bytes = 0;
     bytes += align256(sizeof(T) * FK) * 2;                         // chiW1, chiW2
     bytes += align256(sizeof(T) * KN) * 2;                         // chiH1, chiH2
-    bytes += align256(sizeof(T) * FK * 2 * tl[i].S);               // rowPart
-    bytes += align256(sizeof(T) * KN * 2 * tl[i].R);               // colPart
+    bytes += align256(sizeof(T) * FK * 2 * Smax);                  // rowPart
+    bytes += align256(sizeof(T) * KN * 2 * Rmax);                  // colPart
     bytes += align256(sizeof(T) * K);                              // norms
     off[i + 1] = off[i] + bytes;
     pr[i + 1] = pr[i] + tl[i].rowTilesF * tl[i].S;
@@ -197,12 +215,11 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     P.chiW2 = take(sizeof(T) * FK);
     P.chiH1 = take(sizeof(T) * KN);
     P.chiH2 = take(sizeof(T) * KN);
-    P.rowPart = take(sizeof(T) * FK * 2 * tl[i].S);
-    P.colPart = take(sizeof(T) * KN * 2 * tl[i].R);
+    P.rowPart = take(sizeof(T) * FK * 2 * std::max(tl[i].S, P.tcS));
+    P.colPart = take(sizeof(T) * KN * 2 * std::max(tl[i].R, P.tcR));
     P.norms = take(sizeof(T) * K);
     P.Wt = static_cast<T*>(c->tildeW) + oW;
     P.Ht = static_cast<T*>(c->tildeH) + oH;
-    P.F = F; P.N = N; P.K = K;
     P.S = tl[i].S; P.R = tl[i].R;
     P.rowTilesF = tl[i].rowTilesF; P.colTilesN = tl[i].colTilesN;
     P.chunkN = tl[i].chunkN; P.chunkF = tl[i].chunkF;
@@ -216,20 +233,24 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   pl.count = cnt;
   pl.maxK = maxK;
   int* tabs = nullptr;
-  NMF_TRY(dalloc(c, reinterpret_cast<void**>(&tabs), sizeof(int) * 5 * (cnt + 1)));
+  NMF_TRY(dalloc(c, reinterpret_cast<void**>(&tabs), sizeof(int) * (5 * (cnt + 1) + 4)));
   std::vector<int> all;
   all.insert(all.end(), pr.begin(), pr.end());
   all.insert(all.end(), pc.begin(), pc.end());
   all.insert(all.end(), pw.begin(), pw.end());
   all.insert(all.end(), ph.begin(), ph.end());
   all.insert(all.end(), pk.begin(), pk.end());
+  const int tcRowGrid = probs[0].tcRowTiles * probs[0].tcS, tcColGrid = probs[0].tcColTiles * probs[0].tcR;
+  all.insert(all.end(), {0, c->batched ? 0 : tcRowGrid, 0, c->batched ? 0 : tcColGrid});
   NMF_CU(cudaMemcpy(tabs, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+  pl.d_prefTc = tabs + 5 * (cnt + 1);
   pl.d_prefRow = tabs; pl.totRow = pr[cnt];
   pl.d_prefCol = tabs + (cnt + 1); pl.totCol = pc[cnt];
   pl.d_prefW = tabs + 2 * (cnt + 1); pl.totW = pw[cnt];
   pl.d_prefH = tabs + 3 * (cnt + 1); pl.totH = ph[cnt];
   pl.d_prefK = tabs + 4 * (cnt + 1); pl.totK = pk[cnt];
-  const size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
+  size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
+  if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max(tcRowGrid, tcColGrid));
   NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
   return NMF_OK;
 }
@@ -320,8 +341,9 @@ BetaParams beta_params(const nmf_ctx* c) {
 }
 
 // One or more outer iterations of Algorithm 2 (joint) or Algorithm 1 (alternating).
+// tc: the two sweeps run on the tensor-core kernels (single float problems).
 template <typename T>
-nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLoss) {
+nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLoss, bool tc) {
   const BetaParams bp = beta_params(c);
   cudaStream_t st = c->stream;
   int* status = c->d_status;
@@ -330,6 +352,39 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
                       (c->order == NMF_ORDER_AUTO && c->F[0] >= c->N[0]);
   const int L = c->L;
   const int C = SWEEP_CONTRACT;
+  const int tci = tc ? 1 : 0;
+  auto row_sweep = [&](int wsel, int hsel, int dsel, int flags) -> nmf_status {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc)
+        return cu(timed(&c->timer, st, "tc_row_sweep", 1, [&] {
+          return launch_tc_row_sweep(c->hpf[0], wsel, hsel, dsel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+        }));
+    }
+    return cu(timed(&c->timer, st, "row_sweep", 1, [&] {
+      return launch_row_sweep<T>(pl, wsel, hsel, dsel, flags, bp, lp, status, st);
+    }));
+  };
+  auto col_sweep = [&](int wsel, int hsel, int csel, int flags) -> nmf_status {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc)
+        return cu(timed(&c->timer, st, "tc_col_sweep", 1, [&] {
+          return launch_tc_col_sweep(c->hpf[0], wsel, hsel, csel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+        }));
+    }
+    return cu(timed(&c->timer, st, "col_sweep", 1, [&] {
+      return launch_col_sweep<T>(pl, wsel, hsel, csel, flags, bp, lp, status, st);
+    }));
+  };
+  auto rows_epi = [&](int basesel, int chi) -> nmf_status {
+    return cu(timed(&c->timer, st, "rows_epilogue", 1, [&] {
+      return launch_rows_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
+    }));
+  };
+  auto cols_epi = [&](int basesel, int chi) -> nmf_status {
+    return cu(timed(&c->timer, st, "cols_epilogue", 1, [&] {
+      return launch_cols_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
+    }));
+  };
   for (int it = 0; it < iters; ++it) {
     const bool lossHere = wantLoss && it == iters - 1;
     const int CL = C | (lossHere ? SWEEP_LOSS : 0);
@@ -338,15 +393,15 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
       for (int l = 1; l <= L; ++l) {
         const int f1 = l == 1 ? CL : C;
         if (wfirst) {
-          NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1, bp, lp, status, st); }));
-          NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 1, bp, nullptr, status, st); }));
-          NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_TILDE, SEL_TILDE, OP_CHI, C, bp, lp, status, st); }));
-          NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, l < L, bp, nullptr, status, st); }));
+          NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1));
+          NMF_TRY(rows_epi(SEL_TILDE, 1));
+          NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C));
+          NMF_TRY(cols_epi(SEL_TILDE, l < L));
         } else {
-          NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1, bp, lp, status, st); }));
-          NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 1, bp, nullptr, status, st); }));
-          NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_TILDE, SEL_TILDE, OP_CHI, C, bp, lp, status, st); }));
-          NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, l < L, bp, nullptr, status, st); }));
+          NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1));
+          NMF_TRY(cols_epi(SEL_TILDE, 1));
+          NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C));
+          NMF_TRY(rows_epi(SEL_TILDE, l < L));
         }
       }
     } else {
@@ -355,24 +410,25 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         for (int l = 1; l <= L; ++l) {
           const int fl = (half == 0 && l == 1) ? CL : C;
           if (doW) {
-            NMF_CU(timed(&c->timer, st, "row_sweep", 1, [&] { return launch_row_sweep<T>(pl, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, lp, status, st); }));
-            NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] { return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_CUR, 0, bp, nullptr, status, st); }));
+            NMF_TRY(row_sweep(SEL_CUR, SEL_CUR, OP_SELF, fl));
+            NMF_TRY(rows_epi(SEL_CUR, 0));
           } else {
-            NMF_CU(timed(&c->timer, st, "col_sweep", 1, [&] { return launch_col_sweep<T>(pl, SEL_CUR, SEL_CUR, OP_SELF, fl, bp, lp, status, st); }));
-            NMF_CU(timed(&c->timer, st, "cols_epilogue", 1, [&] { return launch_cols_epilogue<T>(pl, EPI_UPDATE, SEL_CUR, 0, bp, nullptr, status, st); }));
+            NMF_TRY(col_sweep(SEL_CUR, SEL_CUR, OP_SELF, fl));
+            NMF_TRY(cols_epi(SEL_CUR, 0));
           }
         }
       }
     }
     if (c->normalize) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
   }
-  if (wantLoss) c->lossPrefix = wfirst ? 0 : 1;
+  if (wantLoss) c->lossPrefix = (wfirst ? 0 : 1) + (tc ? 2 : 0);
   return NMF_OK;
 }
 
 nmf_status finalize_loss_dense(nmf_ctx* c) {
   const int* pref = nullptr;
   if (c->prec == NMF_FP64) pref = c->lossPrefix == 0 ? c->pd.d_prefRow : c->pd.d_prefCol;
+  else if (c->lossPrefix >= 2) pref = c->pf.d_prefTc + (c->lossPrefix == 2 ? 0 : 2);
   else pref = c->lossPrefix == 0 ? c->pf.d_prefRow : c->pf.d_prefCol;
   return cu(timed(&c->timer, c->stream, "loss_finalize", 1, [&] {
     return launch_loss_finalize(pref, c->count, c->d_lossPart, c->d_lossOut, c->stream);
@@ -442,22 +498,10 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
     if (!wantLoss) return NMF_OK;
     return sync_and_check(c, true, loss_out);
   }
-  if (c->prec == NMF_TF32 || c->prec == NMF_BF16) {
-    if (c->batched || c->L != 1 || !joint) return NMF_EUNSUPPORTED;
-    if (!c->tc) {
-      nmf_status s = tc_create(&c->tc, c->F[0], c->N[0], c->K[0], c->beta, c->kappa,
-                               c->prec == NMF_BF16, c->sms);
-      if (s != NMF_OK) return s;
-    }
-    const bool hfirst = c->order != NMF_W_FIRST;
-    NMF_TRY(tc_step(c->tc, static_cast<const float*>(c->V), c->ldv, static_cast<float*>(c->W),
-                    static_cast<float*>(c->H), iters, wantLoss, c->normalize != 0, hfirst,
-                    c->d_status, c->d_lossOut, &c->timer, c->stream));
-    if (!wantLoss) return NMF_OK;
-    return sync_and_check(c, true, loss_out);
-  }
-  if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss));
-  else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss));
+  const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
+  if (tc && (c->batched || c->prec == NMF_BF16 || tc_kp(c->K[0]) > TC_KPMAX)) return NMF_EUNSUPPORTED;
+  if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss, false));
+  else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss, tc));
   if (!wantLoss) return NMF_OK;
   NMF_TRY(finalize_loss_dense(c));
   return sync_and_check(c, true, loss_out);
@@ -542,7 +586,6 @@ nmf_status nmf_set_options(nmf_ctx* c, nmf_precision precision, nmf_order order,
   if (!(kappa >= 0.0) || !std::isfinite(kappa)) return NMF_EINVAL;
   if (c->sparse && (precision != NMF_FP32 || kappa != 0.0)) return NMF_EINVAL;
   if (precision != c->prec && c->prepared) { cudaStreamSynchronize(c->stream); free_all(c); }
-  if (c->tc && (kappa != c->kappa)) { tc_destroy(c->tc); c->tc = nullptr; }
   c->prec = precision;
   c->order = order;
   c->normalize = normalize ? 1 : 0;
@@ -607,14 +650,6 @@ nmf_status nmf_step_joint(nmf_ctx* c, int32_t iters, double* loss_out) {
 }
 
 nmf_status nmf_step_alternating(nmf_ctx* c, int32_t iters, double* loss_out) {
-  if (c && (c->prec == NMF_TF32 || c->prec == NMF_BF16) && !c->sparse) {
-    // the alternating baseline runs on the SIMT FP32 kernels for tensor-core precisions
-    nmf_precision keep = c->prec;
-    c->prec = NMF_FP32;
-    nmf_status s = step(c, false, iters, loss_out);
-    c->prec = keep;
-    return s;
-  }
   return step(c, false, iters, loss_out);
 }
 

@@ -62,6 +62,13 @@ struct Prob {
   int colTilesN;     // ceil(N / BN)
   int64_t chunkN;    // columns per row-sweep chunk (multiple of BN)
   int64_t chunkF;    // rows per column-sweep chunk (multiple of BF)
+  // tensor-core sweeps (single problems): 128-row / 128-column MMA tiles
+  int tcRowTiles;    // ceil(F / 128)
+  int tcS;           // column chunks of the tensor-core row sweep
+  int tcColTiles;    // ceil(N / 128)
+  int tcR;           // row chunks of the tensor-core column sweep
+  int64_t tcChunkN;  // multiple of 32
+  int64_t tcChunkF;  // multiple of 32
 };
 
 // Finds the problem owning linear block index `b` given an exclusive prefix

@@ -95,6 +95,7 @@ struct Plan {
   int* d_prefW = nullptr; int totW = 0;       // EW-entry blocks over F x K
   int* d_prefH = nullptr; int totH = 0;       // EW-entry blocks over K x N
   int* d_prefK = nullptr; int totK = 0;       // one block per column of W
+  int* d_prefTc = nullptr;                    // {0, tc row grid, 0, tc column grid} (single problem)
 };
 
 template <typename T>
@@ -107,12 +108,15 @@ cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, in
                              cudaStream_t st);
 // W epilogue: W = base . (sum num / sum den)^gamma (mode EPI_UPDATE, base = W or Wt,
 // chi computed from (W_new, Wt) when want_chi) or gout = sum den - sum num (EPI_GRAD).
+// tc != 0: the partials come from the tensor-core sweeps (tcS / tcR slices).
 template <typename T>
 cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st);
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st,
+                                 int tc = 0);
 template <typename T>
 cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st);
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st,
+                                 int tc = 0);
 // Copies W -> Wt and H -> Ht for every problem (skipped once status is set).
 template <typename T>
 cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st);
@@ -126,6 +130,15 @@ cudaError_t launch_loss_finalize(const int* d_prefix, int count, const double* l
 template <typename T>
 cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T* gH,
                        int64_t nH, double* out, cudaStream_t st);
+
+// Tensor-core sweeps (tc_sweeps.cu), single float problems: same operands and
+// partial-sum layout as the SIMT sweeps, with tcS / tcR slices.
+constexpr int TC_KPMAX = 128;  // largest padded rank (multiple of 16) of the tensor-core sweeps
+int tc_kp(int K);              // K padded to a multiple of 16
+cudaError_t launch_tc_row_sweep(const Prob<float>& P, int wsel, int hsel, int dsel, int flags, bool bf16,
+                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+cudaError_t launch_tc_col_sweep(const Prob<float>& P, int wsel, int hsel, int csel, int flags, bool bf16,
+                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
 
 // Sparse beta = 1 path (sparse_kl.cu).
 struct SparseKL {

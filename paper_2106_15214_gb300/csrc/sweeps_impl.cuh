@@ -251,7 +251,7 @@ template <typename T, int BK>
 __global__ void __launch_bounds__(EW)
 rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
-                     int* __restrict__ status) {
+                     int* __restrict__ status, int tc) {
   if (*status) return;
   const int b = blockIdx.x;
   const int pi = find_problem(prefix, count, b);
@@ -260,7 +260,8 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
   const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
   if (idx >= FK) return;
   T num = T(0), den = T(0);
-  for (int s = 0; s < P.S; ++s) {
+  const int slices = tc ? P.tcS : P.S;
+  for (int s = 0; s < slices; ++s) {
     num += P.rowPart[(int64_t)s * 2 * FK + idx];
     den += P.rowPart[(int64_t)s * 2 * FK + FK + idx];
   }
@@ -282,7 +283,7 @@ template <typename T, int BK>
 __global__ void __launch_bounds__(EW)
 cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
-                     int* __restrict__ status) {
+                     int* __restrict__ status, int tc) {
   if (*status) return;
   const int b = blockIdx.x;
   const int pi = find_problem(prefix, count, b);
@@ -291,7 +292,8 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
   const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
   if (idx >= KN) return;
   T num = T(0), den = T(0);
-  for (int r = 0; r < P.R; ++r) {
+  const int slices = tc ? P.tcR : P.R;
+  for (int r = 0; r < slices; ++r) {
     num += P.colPart[(int64_t)r * 2 * KN + idx];
     den += P.colPart[(int64_t)r * 2 * KN + KN + idx];
   }
@@ -476,28 +478,28 @@ cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, in
 
 template <typename T, int BK>
 cudaError_t rows_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                        const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
   rows_epilogue_kernel<T, BK><<<pl.totW, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, mode,
-                                                      basesel, want_chi, bp, gout, status);
+                                                      basesel, want_chi, bp, gout, status, tc);
   return cudaGetLastError();
 }
 template <typename T, int BK>
 cudaError_t cols_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                        const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
   cols_epilogue_kernel<T, BK><<<pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefH, mode,
-                                                      basesel, want_chi, bp, gout, status);
+                                                      basesel, want_chi, bp, gout, status, tc);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
-  NMF_BK_DISPATCH(rows_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st)
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
+  NMF_BK_DISPATCH(rows_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc)
 }
 template <typename T>
 cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st) {
-  NMF_BK_DISPATCH(cols_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st)
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
+  NMF_BK_DISPATCH(cols_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc)
 }
 
 template <typename T>
@@ -530,9 +532,9 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
   template cudaError_t launch_col_sweep<T>(const Plan<T>&, int, int, int, int, const BetaParams&,  \
                                            double*, const int*, cudaStream_t);                     \
   template cudaError_t launch_rows_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
-                                               T*, int*, cudaStream_t);                            \
+                                               T*, int*, cudaStream_t, int);                       \
   template cudaError_t launch_cols_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
-                                               T*, int*, cudaStream_t);                            \
+                                               T*, int*, cudaStream_t, int);                       \
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \

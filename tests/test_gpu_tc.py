@@ -1,0 +1,119 @@
+"""Tensor-core (tcgen05 kind::tf32) path against the FP64 oracle.
+
+TF32 tolerance (derivation in DESIGN.md, "Tolerances"): every operand of the
+three products is rounded to a 10-bit mantissa (u = 2^-11); each product term
+then errs by at most ~2u relative and sums of nonnegative terms keep that
+bound, the elementwise powers scale the error of Vt by |beta - 2|, and the MU
+ratio, gamma and chi compound a few such factors: 1e-2 relative on W, H after
+one iteration bounds it; the objective at the iterate is within 2e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_15214_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BETAS = [-1.0, 0.0, 0.5, 1.0, 1.5, 2.0, 3.0]
+TF32_RTOL = 1e-2
+TF32_LOSS_RTOL = 2e-3
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def problem(F, N, K, seed=0):
+    rng = np.random.default_rng(seed)
+    V = rng.gamma(1.0, 1.0, (F, K)) @ rng.gamma(1.0, 1.0, (K, N)) + 0.05
+    V = V * rng.uniform(0.5, 1.5, (F, N))
+    W0, H0 = inputs.uniform_init(F, N, K, seed=seed + 7)
+    return V, W0, H0
+
+
+def run_tc(V, W0, H0, beta, method="jmm", iters=1, order="W", L=1, kappa=0.0, prec="tf32"):
+    from paper_2106_15214_gb300.binding import NMF
+    F, N = V.shape
+    K = W0.shape[1]
+    m = NMF(F, N, K, beta, precision=prec, order=order, L=L, kappa=kappa)
+    Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
+    m.set_dense(Vd)
+    m.set_factors(Wd, Hd)
+    loss = m.step_joint(iters) if method == "jmm" else m.step_alternating(iters)
+    return Wd.double().cpu().numpy(), Hd.double().cpu().numpy(), loss, m
+
+
+def maxrel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.parametrize("beta", BETAS)
+@pytest.mark.parametrize("method,order", [("jmm", "W"), ("jmm", "H"), ("bmm", "W"), ("bmm", "H")])
+def test_tf32_one_iteration_matches_oracle(lib, beta, method, order):
+    V, W0, H0 = problem(200, 300, 20, seed=1)     # 2 row tiles of 128, 3 column tiles, ragged
+    W, H, loss, m = run_tc(V, W0, H0, beta, method, 1, order)
+    Wo, Ho, lo = O.run(V, W0, H0, beta, method=method, iters=1, order=order)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[0], rel=TF32_LOSS_RTOL)
+
+
+@pytest.mark.parametrize("K", [1, 7, 16, 33, 64, 100, 128])
+def test_tf32_ranks(lib, K):
+    V, W0, H0 = problem(150, 170, K, seed=2)
+    for beta in (0.0, 1.5):
+        W, H, loss, _ = run_tc(V, W0, H0, beta, "jmm", 1, "W")
+        Wo, Ho, lo = O.run(V, W0, H0, beta, iters=1)
+        assert maxrel(W, Wo) < TF32_RTOL, K
+        assert maxrel(H, Ho) < TF32_RTOL, K
+
+
+@pytest.mark.parametrize("order", ["W", "H"])
+def test_tf32_subiterations_and_kappa(lib, order):
+    V, W0, H0 = problem(140, 260, 12, seed=3)
+    for beta in (0.0, 1.0, 2.5):
+        W, H, _, _ = run_tc(V, W0, H0, beta, "jmm", 1, order, L=2, kappa=0.01)
+        Wo, Ho, _ = O.run(V, W0, H0, beta, iters=1, order=order, L=2, kappa=0.01)
+        assert maxrel(W, Wo) < TF32_RTOL
+        assert maxrel(H, Ho) < TF32_RTOL
+
+
+def test_tf32_agrees_with_fp32_path(lib):
+    V, W0, H0 = problem(300, 400, 24, seed=4)
+    W, H, l, _ = run_tc(V, W0, H0, 0.0, "jmm", 5, "H")
+    W2, H2, l2, _ = run_tc(V, W0, H0, 0.0, "jmm", 5, "H", prec="fp32")
+    assert maxrel(W, W2) < 3e-2 and maxrel(H, H2) < 3e-2
+    assert l == pytest.approx(l2, rel=5e-3)
+
+
+def test_tf32_descends(lib):
+    V, W0, H0 = problem(256, 384, 16, seed=5)
+    from paper_2106_15214_gb300.binding import NMF
+    m = NMF(256, 384, 16, 1.0, precision="tf32")
+    Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
+    m.set_dense(Vd)
+    m.set_factors(Wd, Hd)
+    losses = [m.step_joint(1) for _ in range(60)]
+    d = np.diff(losses)
+    assert losses[-1] < 0.5 * losses[0]
+    assert np.all(d <= 1e-3 * np.abs(np.array(losses[1:])))
+
+
+def test_tf32_faces_full_size(lib):
+    p = inputs.dense_quadratic_faces()
+    W, H, loss, _ = run_tc(p.V, p.W0, p.H0, 2.0, "jmm", 1, "W")
+    Wo, Ho, lo = O.run(p.V, p.W0, p.H0, 2.0, iters=1)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[0], rel=TF32_LOSS_RTOL)
+
+
+def test_tf32_spectrogram_full_size(lib):
+    p = inputs.dense_is_spectrogram()
+    W, H, loss, _ = run_tc(p.V, p.W0, p.H0, 0.0, "jmm", 1, "H")
+    Wo, Ho, lo = O.run(p.V, p.W0, p.H0, 0.0, iters=1, order="H")
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[0], rel=TF32_LOSS_RTOL)
