@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <type_traits>
@@ -70,6 +71,19 @@ struct nmf_ctx {
   void* stageH = nullptr;
   SparseKL sp;
   Timer timer;
+  TcMaps tcmaps;
+  // CUDA graphs of step calls (see capture_step)
+  struct GraphEntry {
+    uint64_t key = 0;
+    cudaGraphExec_t exec = nullptr;
+    Timer::Sink sink;
+    const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // data captured with
+  };
+  std::vector<GraphEntry> graphs;
+  std::vector<uint64_t> seenKeys;
+  bool useGraphs = true;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t evIn = nullptr, evOut = nullptr;
   int sms = 148;
 };
 
@@ -86,7 +100,10 @@ nmf_status cu(cudaError_t e) { return e == cudaSuccess ? NMF_OK : NMF_ECUDA; }
   } while (0)
 #define NMF_CU(x) NMF_TRY(cu(x))
 
+void invalidate_graphs(nmf_ctx* c);
+
 void free_all(nmf_ctx* c) {
+  invalidate_graphs(c);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -148,17 +165,35 @@ bool data_ready(const nmf_ctx* c) {
 }
 
 // Tensor-core sweeps: 128-row (row sweep) or 128-column (column sweep) MMA
-// tiles, split along the other dimension into chunks of 32-wide tiles until
-// about one block per SM.
+// tiles, split along the streamed dimension into chunks of 32-wide tiles.
+// The split minimises an estimate of the sweep's time in tile units: waves of
+// one block per SM times (tiles per block + a fixed per-block cost of two
+// tiles for set-up and the partial-sum write). NMF_TC_TARGET=<blocks> forces
+// about that many blocks instead (for tuning).
+int64_t best_split(int64_t fixedTiles, int64_t streamTiles, int sms) {
+  const char* env = std::getenv("NMF_TC_TARGET");
+  if (env && std::atoi(env) > 0) {
+    const int64_t target = std::atoi(env);
+    return std::min<int64_t>(std::max<int64_t>(1, cdiv(target, fixedTiles)), streamTiles);
+  }
+  int64_t best = 1;
+  double bestCost = 1e300;
+  for (int64_t S = 1; S <= std::min<int64_t>(streamTiles, 64); ++S) {
+    const double waves = (double)cdiv(fixedTiles * S, sms);
+    const double cost = waves * ((double)cdiv(streamTiles, S) + 2.0);
+    if (cost < bestCost - 1e-9) { bestCost = cost; best = S; }
+  }
+  return best;
+}
+
 void tc_tiling(Prob<float>& P, int sms) {
-  const int64_t target = sms;
   const int64_t nT = cdiv(P.N, 32), fT = cdiv(P.F, 32);
   P.tcRowTiles = (int)cdiv(P.F, 128);
-  int64_t S = std::min<int64_t>(std::max<int64_t>(1, cdiv(target, P.tcRowTiles)), nT);
+  const int64_t S = best_split(P.tcRowTiles, nT, sms);
   P.tcChunkN = cdiv(nT, S) * 32;
   P.tcS = (int)cdiv(P.N, P.tcChunkN);
   P.tcColTiles = (int)cdiv(P.N, 128);
-  int64_t R = std::min<int64_t>(std::max<int64_t>(1, cdiv(target, P.tcColTiles)), fT);
+  const int64_t R = best_split(P.tcColTiles, fT, sms);
   P.tcChunkF = cdiv(fT, R) * 32;
   P.tcR = (int)cdiv(P.F, P.tcChunkF);
 }
@@ -226,6 +261,26 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     P.V = nullptr; P.W = nullptr; P.H = nullptr;
     P.ldv = c->batched ? N : c->ldv;
     oW += FK; oH += KN; oV += (size_t)F * N;
+  }
+  // TF32 operand shadows for the tensor-core sweeps (single float problems)
+  if (!c->batched && sizeof(T) == 4 && (c->prec == NMF_TF32 || c->prec == NMF_BF16)) {
+    Prob<T>& P = probs[0];
+    P.kp = (P.K + 15) & ~15;
+    P.ks = (P.kp + 31) & ~31;
+    P.Fp = (P.F + 3) & ~int64_t(3);
+    P.Np = (P.N + 3) & ~int64_t(3);
+    const size_t nWS = (size_t)P.F * P.ks, nT = (size_t)P.kp * P.Fp, nHT = (size_t)P.N * P.ks, nH = (size_t)P.kp * P.Np;
+    const size_t parts[8] = {nWS, nT, nHT, nH, nT, nT, nH, nH};
+    size_t total = 0;
+    for (size_t q : parts) total += align256(sizeof(T) * q);
+    void* sh = nullptr;
+    NMF_TRY(dalloc(c, &sh, total));
+    NMF_CU(cudaMemset(sh, 0, total));
+    T* ptrs[8];
+    char* cur = static_cast<char*>(sh);
+    for (int q = 0; q < 8; ++q) { ptrs[q] = reinterpret_cast<T*>(cur); cur += align256(sizeof(T) * parts[q]); }
+    P.sWS = ptrs[0]; P.sWT = ptrs[1]; P.sHT = ptrs[2]; P.sHS = ptrs[3];
+    P.sCW1 = ptrs[4]; P.sCW2 = ptrs[5]; P.sCH1 = ptrs[6]; P.sCH2 = ptrs[7];
   }
   void* d = nullptr;
   NMF_TRY(dalloc(c, &d, sizeof(Prob<T>) * cnt));
@@ -320,6 +375,8 @@ nmf_status prepare(nmf_ctx* c) {
     // alternating baseline run on the FP32 SIMT kernels.
     if (c->prec == NMF_FP64) NMF_TRY(build_plan<double>(c, c->pd, c->hpd));
     else NMF_TRY(build_plan<float>(c, c->pf, c->hpf));
+    c->tcmaps.ok = false;
+    if (c->prec != NMF_FP64 && !c->batched && c->hpf[0].sWS) tc_build_maps(c->hpf[0], &c->tcmaps);
     c->prepared = true;
     c->tableDirty = true;
   }
@@ -337,6 +394,7 @@ BetaParams beta_params(const nmf_ctx* c) {
   bp.gamma = gamma_of(c->beta);
   bp.kappa = c->kappa;
   bp.kind = beta_kind(c->beta);
+  fill_series(bp);
   return bp;
 }
 
@@ -357,7 +415,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
         return cu(timed(&c->timer, st, "tc_row_sweep", 1, [&] {
-          return launch_tc_row_sweep(c->hpf[0], wsel, hsel, dsel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+          return launch_tc_row_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, dsel, flags, c->prec == NMF_BF16, bp, lp, status, st);
         }));
     }
     return cu(timed(&c->timer, st, "row_sweep", 1, [&] {
@@ -368,22 +426,34 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
         return cu(timed(&c->timer, st, "tc_col_sweep", 1, [&] {
-          return launch_tc_col_sweep(c->hpf[0], wsel, hsel, csel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+          return launch_tc_col_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, csel, flags, c->prec == NMF_BF16, bp, lp, status, st);
         }));
     }
     return cu(timed(&c->timer, st, "col_sweep", 1, [&] {
       return launch_col_sweep<T>(pl, wsel, hsel, csel, flags, bp, lp, status, st);
     }));
   };
+  // tensor-core mode: TF32 shadows of the factors the next sweep reads
+  auto shadows = [&](int which) -> nmf_status {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc && c->hpf[0].sWS)
+        return cu(timed(&c->timer, st, "shadow_factors", 1, [&] {
+          return launch_shadow_factors<float>(c->hpf[0], which, status, st);
+        }));
+    }
+    return NMF_OK;
+  };
   auto rows_epi = [&](int basesel, int chi) -> nmf_status {
-    return cu(timed(&c->timer, st, "rows_epilogue", 1, [&] {
+    NMF_TRY(cu(timed(&c->timer, st, "rows_epilogue", 1, [&] {
       return launch_rows_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
-    }));
+    })));
+    return basesel == SEL_CUR ? shadows(1) : NMF_OK;   // alternating: the new W feeds the next sweep
   };
   auto cols_epi = [&](int basesel, int chi) -> nmf_status {
-    return cu(timed(&c->timer, st, "cols_epilogue", 1, [&] {
+    NMF_TRY(cu(timed(&c->timer, st, "cols_epilogue", 1, [&] {
       return launch_cols_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
-    }));
+    })));
+    return basesel == SEL_CUR ? shadows(2) : NMF_OK;
   };
   for (int it = 0; it < iters; ++it) {
     const bool lossHere = wantLoss && it == iters - 1;
@@ -435,22 +505,29 @@ nmf_status finalize_loss_dense(nmf_ctx* c) {
   }));
 }
 
-// Synchronises; on a device-side non-finite flag restores W, H from the tilde copies.
-nmf_status sync_and_check(nmf_ctx* c, bool readLoss, double* loss_out) {
+// Copies the loss (when asked) and the status word into pinned host memory.
+nmf_status enqueue_readback(nmf_ctx* c, bool readLoss) {
   const int cnt = c->count;
   if (readLoss)
     NMF_CU(cudaMemcpyAsync(c->h_pinned, c->d_lossOut, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
-  int* hs = reinterpret_cast<int*>(c->h_pinned + cnt + 1);
-  NMF_CU(cudaMemcpyAsync(hs, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  NMF_CU(cudaStreamSynchronize(c->stream));
-  if (*hs != 0) {
+  NMF_CU(cudaMemcpyAsync(reinterpret_cast<int*>(c->h_pinned + cnt + 1), c->d_status, sizeof(int),
+                         cudaMemcpyDeviceToHost, c->stream));
+  return NMF_OK;
+}
+
+// After the stream `sync` has completed the readback: on a device-side
+// non-finite flag restores W, H from the tilde copies; else publishes the loss.
+nmf_status complete_readback(nmf_ctx* c, bool readLoss, double* loss_out) {
+  const int cnt = c->count;
+  const int hs = *reinterpret_cast<int*>(c->h_pinned + cnt + 1);
+  if (hs != 0) {
     const size_t es = c->sparse ? 4 : esize(c);
     void* W = c->batched ? c->Wp : c->W;
     void* H = c->batched ? c->Hp : c->H;
     NMF_CU(cudaMemcpyAsync(W, c->tildeW, es * c->elemsW, cudaMemcpyDeviceToDevice, c->stream));
     NMF_CU(cudaMemcpyAsync(H, c->tildeH, es * c->elemsH, cudaMemcpyDeviceToDevice, c->stream));
     NMF_CU(cudaStreamSynchronize(c->stream));
-    return (nmf_status)*hs;
+    return (nmf_status)hs;
   }
   if (readLoss) {
     c->lastLosses.assign(c->h_pinned, c->h_pinned + cnt);
@@ -462,6 +539,13 @@ nmf_status sync_and_check(nmf_ctx* c, bool readLoss, double* loss_out) {
     }
   }
   return NMF_OK;
+}
+
+// Synchronises; on a device-side non-finite flag restores W, H from the tilde copies.
+nmf_status sync_and_check(nmf_ctx* c, bool readLoss, double* loss_out) {
+  NMF_TRY(enqueue_readback(c, readLoss));
+  NMF_CU(cudaStreamSynchronize(c->stream));
+  return complete_readback(c, readLoss, loss_out);
 }
 
 // Sparse contexts: binds the caller's CSR arrays and builds the CSC copy once
@@ -481,13 +565,10 @@ nmf_status ensure_sparse(nmf_ctx* c) {
   return NMF_OK;
 }
 
-nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
-  if (!c || iters < 1) return NMF_EINVAL;
-  if (!data_ready(c)) return NMF_ENOTREADY;
-  NMF_TRY(prepare(c));
-  const bool wantLoss = loss_out != nullptr;
+// Every kernel and copy of one step call, enqueued on c->stream (no host
+// synchronisation, no allocation: the sequence can be captured into a graph).
+nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss) {
   if (c->sparse) {
-    NMF_TRY(ensure_sparse(c));
     const bool hfirst = c->order == NMF_H_FIRST || (c->order == NMF_ORDER_AUTO && c->F[0] < c->N[0]);
     for (int it = 0; it < iters; ++it) {
       const bool lossHere = wantLoss && it == iters - 1;
@@ -495,16 +576,118 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
                          lossHere, c->normalize != 0, c->d_status, &c->timer, c->stream));
     }
     if (wantLoss) NMF_CU(cudaMemcpyAsync(c->d_lossOut, c->sp.sums, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    if (!wantLoss) return NMF_OK;
-    return sync_and_check(c, true, loss_out);
+  } else {
+    const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
+    if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss, false));
+    else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss, tc));
+    if (wantLoss) NMF_TRY(finalize_loss_dense(c));
   }
-  const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
-  if (tc && (c->batched || c->prec == NMF_BF16 || tc_kp(c->K[0]) > TC_KPMAX)) return NMF_EUNSUPPORTED;
-  if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss, false));
-  else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss, tc));
+  return enqueue_readback(c, wantLoss);
+}
+
+// ---- CUDA graphs --------------------------------------------------------------
+// A step configuration seen once runs eagerly; from its second call on it is
+// captured once (on the context's own stream) and replayed with one launch.
+// The caller's stream and the context stream are ordered with events, so the
+// call stays stream-ordered on the caller's stream.
+
+uint64_t step_key(const nmf_ctx* c, bool joint, int iters, bool wantLoss) {
+  uint64_t k = (uint64_t)(uint32_t)iters;
+  k = k * 4 + (joint ? 1 : 0) + (wantLoss ? 2 : 0);
+  k = k * 2 + (c->timer.on ? 1 : 0);
+  return k;
+}
+
+void invalidate_graphs(nmf_ctx* c) {
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& p : g.sink.pairs) { c->timer.pool.push_back(p.a); c->timer.pool.push_back(p.b); }
+  }
+  c->graphs.clear();
+  c->seenKeys.clear();
+}
+
+nmf_status ensure_graph_stream(nmf_ctx* c) {
+  if (c->gs) return NMF_OK;
+  if (cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return NMF_ECUDA; }
+  if (cudaEventCreateWithFlags(&c->evIn, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->evOut, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return NMF_ECUDA;
+  }
+  return NMF_OK;
+}
+
+// Captures enqueue_step into a graph; returns nullptr (graphs then stay off
+// for this context) if capture is not possible.
+nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t iters, bool wantLoss) {
+  if (ensure_graph_stream(c) != NMF_OK) return nullptr;
+  cudaStream_t user = c->stream;
+  nmf_ctx::GraphEntry e;
+  e.key = key;
+  const void* ptrs[6] = {c->V, c->W, c->H, c->Vp, c->Wp, c->Hp};
+  std::copy(ptrs, ptrs + 6, e.ptrs);
+  c->stream = c->gs;
+  c->timer.sink = &e.sink;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  nmf_status st = ok ? enqueue_step(c, joint, iters, wantLoss) : NMF_ECUDA;
+  if (ok) ok = cudaStreamEndCapture(c->gs, &graph) == cudaSuccess && st == NMF_OK && graph;
+  if (ok) ok = cudaGraphInstantiate(&e.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  c->timer.sink = nullptr;
+  c->stream = user;
+  if (!ok) {
+    cudaGetLastError();
+    for (auto& p : e.sink.pairs) { c->timer.pool.push_back(p.a); c->timer.pool.push_back(p.b); }
+    c->useGraphs = false;
+    return nullptr;
+  }
+  c->graphs.push_back(std::move(e));
+  return &c->graphs.back();
+}
+
+nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* loss_out) {
+  NMF_CU(cudaEventRecord(c->evIn, c->stream));
+  NMF_CU(cudaStreamWaitEvent(c->gs, c->evIn, 0));
+  NMF_CU(cudaGraphLaunch(g.exec, c->gs));
+  NMF_CU(cudaEventRecord(c->evOut, c->gs));
+  NMF_CU(cudaStreamWaitEvent(c->stream, c->evOut, 0));
+  if (c->timer.on || wantLoss) NMF_CU(cudaStreamSynchronize(c->gs));
+  c->timer.credit(g.sink, c->timer.on);
   if (!wantLoss) return NMF_OK;
-  NMF_TRY(finalize_loss_dense(c));
-  return sync_and_check(c, true, loss_out);
+  return complete_readback(c, true, loss_out);
+}
+
+nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
+  if (!c || iters < 1) return NMF_EINVAL;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  NMF_TRY(prepare(c));
+  if (c->sparse) NMF_TRY(ensure_sparse(c));
+  const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
+  if (!c->sparse && tc && (c->batched || c->prec == NMF_BF16 || tc_kp(c->K[0]) > TC_KPMAX))
+    return NMF_EUNSUPPORTED;
+  const bool wantLoss = loss_out != nullptr;
+  if (c->useGraphs && c->stream != c->gs) {
+    const uint64_t key = step_key(c, joint, iters, wantLoss);
+    const void* ptrs[6] = {c->V, c->W, c->H, c->Vp, c->Wp, c->Hp};
+    for (auto& g : c->graphs)
+      if (!std::equal(ptrs, ptrs + 6, g.ptrs)) { invalidate_graphs(c); break; }
+    for (auto& g : c->graphs)
+      if (g.key == key) return replay(c, g, wantLoss, loss_out);
+    bool seen = false;
+    for (uint64_t k : c->seenKeys) seen = seen || k == key;
+    if (seen) {
+      nmf_ctx::GraphEntry* g = capture_step(c, key, joint, iters, wantLoss);
+      if (g) return replay(c, *g, wantLoss, loss_out);
+    } else {
+      c->seenKeys.push_back(key);
+    }
+  }
+  NMF_TRY(enqueue_step(c, joint, iters, wantLoss));
+  if (!wantLoss) return NMF_OK;
+  NMF_CU(cudaStreamSynchronize(c->stream));
+  return complete_readback(c, true, loss_out);
 }
 
 bool valid_beta(double b) { return std::isfinite(b); }
@@ -586,6 +769,7 @@ nmf_status nmf_set_options(nmf_ctx* c, nmf_precision precision, nmf_order order,
   if (!(kappa >= 0.0) || !std::isfinite(kappa)) return NMF_EINVAL;
   if (c->sparse && (precision != NMF_FP32 || kappa != 0.0)) return NMF_EINVAL;
   if (precision != c->prec && c->prepared) { cudaStreamSynchronize(c->stream); free_all(c); }
+  invalidate_graphs(c);
   c->prec = precision;
   c->order = order;
   c->normalize = normalize ? 1 : 0;
@@ -598,12 +782,14 @@ nmf_status nmf_set_options(nmf_ctx* c, nmf_precision precision, nmf_order order,
 nmf_status nmf_set_subiterations(nmf_ctx* c, int32_t L) {
   if (!c || L < 1) return NMF_EINVAL;
   if (c->sparse && L != 1) return NMF_EUNSUPPORTED;
+  invalidate_graphs(c);
   c->L = L;
   return NMF_OK;
 }
 
 nmf_status nmf_set_dense(nmf_ctx* c, const void* V_dev, int64_t ldv) {
   if (!c || !V_dev || c->batched || c->sparse || ldv < c->N[0]) return NMF_EINVAL;
+  invalidate_graphs(c);
   c->V = V_dev;
   c->ldv = ldv;
   c->tableDirty = true;
@@ -617,6 +803,7 @@ nmf_status nmf_set_csr(nmf_ctx* c, int64_t nnz, const int32_t* rowptr, const int
   if (nnz >= ((int64_t)1 << 31)) return NMF_EUNSUPPORTED;
   if (c->V) return NMF_EINVAL;
   if (c->prepared) { cudaStreamSynchronize(c->stream); free_all(c); }
+  invalidate_graphs(c);
   c->sparse = true;
   c->nnz = nnz;
   c->rowptr = rowptr; c->col = col; c->val = val;
@@ -626,6 +813,7 @@ nmf_status nmf_set_csr(nmf_ctx* c, int64_t nnz, const int32_t* rowptr, const int
 
 nmf_status nmf_set_factors(nmf_ctx* c, void* W_dev, void* H_dev) {
   if (!c || !W_dev || !H_dev || c->batched) return NMF_EINVAL;
+  invalidate_graphs(c);
   c->W = W_dev;
   c->H = H_dev;
   c->tableDirty = true;
@@ -637,6 +825,7 @@ nmf_status nmf_set_factors(nmf_ctx* c, void* W_dev, void* H_dev) {
 
 nmf_status nmf_batch_set_packed(nmf_ctx* c, const void* V_packed, void* W_packed, void* H_packed) {
   if (!c || !c->batched || !V_packed || !W_packed || !H_packed) return NMF_EINVAL;
+  invalidate_graphs(c);
   c->Vp = V_packed; c->Wp = W_packed; c->Hp = H_packed;
   c->tableDirty = true;
   if (c->d_status) {
@@ -801,6 +990,7 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
 
 nmf_status nmf_set_timing(nmf_ctx* c, int enable) {
   if (!c) return NMF_EINVAL;
+  invalidate_graphs(c);
   c->timer.on = enable != 0;
   return NMF_OK;
 }
@@ -834,7 +1024,11 @@ nmf_status nmf_reset_timing(nmf_ctx* c) {
 void nmf_destroy(nmf_ctx* c) {
   if (!c) return;
   if (c->prepared) cudaStreamSynchronize(c->stream);
+  if (c->gs) cudaStreamSynchronize(c->gs);
   free_all(c);
+  if (c->gs) cudaStreamDestroy(c->gs);
+  if (c->evIn) cudaEventDestroy(c->evIn);
+  if (c->evOut) cudaEventDestroy(c->evOut);
   delete c;
 }
 

@@ -36,7 +36,18 @@ struct BetaParams {
   double gamma;
   double kappa;
   int kind;
+  float series[7];  // Taylor coefficients of phi_beta(u) for u^2 .. u^8 (fill_series)
 };
+
+// phi_b(u) = ((1+u)^b - 1 - b u) / (b (b-1)) = sum_{j>=2} c_j u^j with
+// c_2 = 1/2 and c_{j+1} = c_j (b - j) / (j + 1); computed once on the host.
+inline void fill_series(BetaParams& bp) {
+  double c = 0.5;
+  for (int j = 2; j <= 8; ++j) {
+    bp.series[j - 2] = (float)c;
+    c *= (bp.beta - (double)j) / (double)(j + 1);
+  }
+}
 
 // One problem of a (possibly batched) context. Every pointer is device memory.
 template <typename T>
@@ -69,6 +80,19 @@ struct Prob {
   int tcR;           // row chunks of the tensor-core column sweep
   int64_t tcChunkN;  // multiple of 32
   int64_t tcChunkF;  // multiple of 32
+  // TF32-rounded, zero-padded operand copies read by TMA in the tensor-core
+  // sweeps (null outside tensor-core contexts). kp = K rounded up to 16,
+  // ks = kp rounded up to 32, Fp / Np = F / N rounded up to 4 (16-byte rows).
+  T* sWS;    // [F][ks]  W
+  T* sWT;    // [kp][Fp] W transposed
+  T* sHT;    // [N][ks]  H transposed
+  T* sHS;    // [kp][Np] H
+  T* sCW1;   // [kp][Fp] chi_1(W, Wt) transposed
+  T* sCW2;   // [kp][Fp] chi_2(W, Wt) transposed
+  T* sCH1;   // [kp][Np] chi_1(H, Ht)
+  T* sCH2;   // [kp][Np] chi_2(H, Ht)
+  int kp, ks;
+  int64_t Fp, Np;
 };
 
 // Finds the problem owning linear block index `b` given an exclusive prefix
@@ -151,23 +175,22 @@ __device__ __forceinline__ double dbeta_direct(double x, double y, double beta, 
 
 // Float: d = y^b phi_b(u) with u = x/y - 1 and
 // phi_b(u) = ((1+u)^b - 1 - b u) / (b (b-1)); near u = 0 the Taylor series
-// u^2/2 + (b-2)u^3/6 + (b-2)(b-3)u^4/24 + ... avoids the cancellation that
-// the printed formula suffers in single precision. beta = 1 and 0 are the
-// limits (1+u) log1p(u) - u and u - log1p(u).
-__device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int bk) {
+// u^2/2 + (b-2)u^3/6 + (b-2)(b-3)u^4/24 + ... (coefficients in bp.series)
+// avoids the cancellation that the printed formula suffers in single
+// precision. beta = 1 and 0 are the limits (1+u) log1p(u) - u and u - log1p(u).
+__device__ __forceinline__ float series_phi(float u, const float* c) {
+  float s = c[6];
+  #pragma unroll
+  for (int j = 5; j >= 0; --j) s = fmaf(s, u, c[j]);
+  return s * u * u;
+}
+__device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int bk, const float* c) {
   if (bk == BK_EUC) { float d = x - y; return 0.5f * d * d; }
   if (bk == BK_KL && x <= 0.0f) return y;
   float u = (x - y) / y;
   float phi;
   if (fabsf(u) < 0.1f) {
-    float c = 0.5f, s = 0.0f, up = u * u;
-    #pragma unroll
-    for (int j = 2; j <= 8; ++j) {   // coefficient of u^j: prod_{i=2}^{j-1} (b - i) / j!
-      s += c * up;
-      up *= u;
-      c *= (beta - float(j)) / float(j + 1);
-    }
-    phi = s;
+    phi = series_phi(u, c);
   } else if (bk == BK_KL) {
     phi = (1.0f + u) * log1pf(u) - u;
   } else if (bk == BK_IS) {
@@ -179,13 +202,53 @@ __device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int 
   return yb * phi;
 }
 
+// Round to the nearest TF32 value (10-bit mantissa), kept in the container type.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double tf32_round(double x) { return (double)tf32_round((float)x); }
+
+// ---- hardware approximations for the TF32 tensor-core path -------------------
+// (the operands there are rounded to 10-bit mantissas, far coarser than these)
+__device__ __forceinline__ float rcp_fast(float x) { float r; asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float lg2_fast(float x) { float r; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float ex2_fast(float x) { float r; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float rsqrt_fast(float x) { float r; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+
+template <int BK>
+__device__ __forceinline__ void ab_terms_fast(float v, float vt, float bm2, float& A, float& B) {
+  if (BK == BK_KL) { A = v * rcp_fast(vt); B = 1.f; }
+  else if (BK == BK_EUC) { A = v; B = vt; }
+  else if (BK == BK_IS) { const float r = rcp_fast(vt); B = r; A = v * r * r; }
+  else if (BK == BK_B15) { const float r = rsqrt_fast(vt); A = v * r; B = vt * r; }
+  else { const float p = ex2_fast(bm2 * lg2_fast(vt)); A = v * p; B = vt * p; }
+}
+
+// Same stable form with the approximations above (natural log = lg2 * ln 2).
+template <int BK>
+__device__ __forceinline__ float dbeta_fast(float x, float y, float beta, const float* c) {
+  constexpr float LN2 = 0.69314718056f;
+  if (BK == BK_EUC) { const float d = x - y; return 0.5f * d * d; }
+  if (BK == BK_KL && x <= 0.0f) return y;
+  const float u = (x - y) * rcp_fast(y);
+  float phi;
+  if (fabsf(u) < 0.1f) phi = series_phi(u, c);
+  else if (BK == BK_KL) phi = (1.0f + u) * (LN2 * lg2_fast(1.0f + u)) - u;
+  else if (BK == BK_IS) phi = u - LN2 * lg2_fast(1.0f + u);
+  else phi = (ex2_fast(beta * lg2_fast(1.0f + u)) - 1.0f - beta * u) * rcp_fast(beta * (beta - 1.0f));
+  const float yb = (BK == BK_KL) ? y : (BK == BK_IS ? 1.0f : ex2_fast(beta * lg2_fast(y)));
+  return yb * phi;
+}
+
 template <typename T> struct DB;
 template <> struct DB<double> {
-  __device__ static double eval(double x, double y, double beta, int bk) { return dbeta_direct(x, y, beta, bk); }
+  __device__ static double eval(double x, double y, const BetaParams& bp, int bk) { return dbeta_direct(x, y, bp.beta, bk); }
 };
 template <> struct DB<float> {
-  __device__ static double eval(float x, float y, double beta, int bk) {
-    return (double)dbeta_stable(x, y, (float)beta, bk);
+  __device__ static double eval(float x, float y, const BetaParams& bp, int bk) {
+    return (double)dbeta_stable(x, y, (float)bp.beta, bk, bp.series);
   }
 };
 

@@ -1,9 +1,12 @@
 // internal.h -- host-side declarations shared by the translation units of libnmf.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -17,15 +20,19 @@ constexpr int EW = 256;    // entries per elementwise block
 constexpr int KMAX = 128;  // largest rank the SIMT kernels accept
 
 // Per-context launch counting and optional CUDA-event timing of each kernel
-// (nmf_set_timing / nmf_get_timing). Event pairs are resolved lazily.
+// (nmf_set_timing / nmf_get_timing). Event pairs are resolved lazily. While a
+// step is being captured into a CUDA graph, launch counts and event pairs go
+// to the graph's own lists (`sink`) and are credited on every replay.
 struct Timer {
   struct Rec { const char* name; int64_t launches; double ms; };
   struct Pending { cudaEvent_t a, b; int rec; };
+  struct Sink { std::vector<std::pair<int, int>> counts; std::vector<Pending> pairs; };
   bool on = false;
   int64_t total = 0;
   std::vector<Rec> recs;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  Sink* sink = nullptr;
 
   int rec_index(const char* name) {
     for (size_t i = 0; i < recs.size(); ++i)
@@ -39,7 +46,7 @@ struct Timer {
     if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
     return e;
   }
-  // Adds the elapsed time of every recorded pair (the stream must be synchronised).
+  // Adds the elapsed time of every recorded eager pair (the stream must be synchronised).
   void resolve() {
     for (auto& p : pending) {
       float ms = 0.f;
@@ -50,7 +57,17 @@ struct Timer {
     }
     pending.clear();
   }
-  void reset() { resolve(); recs.clear(); total = 0; }
+  // Credits one replay of a captured graph (its events must have completed).
+  void credit(const Sink& g, bool withTimes) {
+    for (auto& c : g.counts) { recs[c.first].launches += c.second; total += c.second; }
+    if (!withTimes) return;
+    for (auto& p : g.pairs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) recs[p.rec].ms += ms;
+      else cudaGetLastError();
+    }
+  }
+  void reset() { resolve(); for (auto& r : recs) { r.launches = 0; r.ms = 0.0; } total = 0; }
   ~Timer() {
     for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : pool) cudaEventDestroy(e);
@@ -62,8 +79,8 @@ template <typename Fn>
 inline cudaError_t timed(Timer* t, cudaStream_t st, const char* name, int nkern, Fn&& fn) {
   if (!t) return fn();
   const int r = t->rec_index(name);
-  t->recs[r].launches += nkern;
-  t->total += nkern;
+  if (t->sink) t->sink->counts.push_back({r, nkern});
+  else { t->recs[r].launches += nkern; t->total += nkern; }
   cudaEvent_t a = nullptr, b = nullptr;
   if (t->on) {
     a = t->get();
@@ -73,8 +90,25 @@ inline cudaError_t timed(Timer* t, cudaStream_t st, const char* name, int nkern,
   cudaError_t e = fn();
   if (t->on && a && b) {
     cudaEventRecord(b, st);
-    t->pending.push_back({a, b, r});
+    if (t->sink) t->sink->pairs.push_back({a, b, r});
+    else t->pending.push_back({a, b, r});
   }
+  return e;
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device (kept out of
+// CUDA-graph capture, which replays launches only).
+inline cudaError_t ensure_smem_attr(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mtx;
+  static std::vector<std::tuple<const void*, int, size_t>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+  std::lock_guard<std::mutex> lock(mtx);
+  for (auto& t : done)
+    if (std::get<0>(t) == func && std::get<1>(t) == dev && std::get<2>(t) >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.emplace_back(func, dev, bytes);
   return e;
 }
 
@@ -126,19 +160,39 @@ cudaError_t launch_normalize(const Plan<T>& pl, const int* status, cudaStream_t 
 // out[i] = fixed-order sum of lossPart over problem i's blocks of the given prefix table.
 cudaError_t launch_loss_finalize(const int* d_prefix, int count, const double* lossPart,
                                  double* out, cudaStream_t st);
+// TF32 shadows of the current W (which & 1) / H (which & 2) for the tensor-core sweeps.
+template <typename T>
+cudaError_t launch_shadow_factors(const Prob<T>& P, int which, const int* status, cudaStream_t st);
 // KKT residual sums: out[0] = sum |min(W, gW)|, out[1] = sum |min(H, gH)| (single problem).
 template <typename T>
 cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T* gH,
                        int64_t nH, double* out, cudaStream_t st);
 
-// Tensor-core sweeps (tc_sweeps.cu), single float problems: same operands and
-// partial-sum layout as the SIMT sweeps, with tcS / tcR slices.
+// Tensor-core sweeps, single float problems: same operands and partial-sum
+// layout as the SIMT sweeps, with tcS / tcR slices. kp <= 64 runs the
+// warp-specialised kernels (tc_ws.cu) on TMA loads of the TF32 shadows;
+// 64 < kp <= 128 the simpler kernels of tc_sweeps.cu.
 constexpr int TC_KPMAX = 128;  // largest padded rank (multiple of 16) of the tensor-core sweeps
 int tc_kp(int K);              // K padded to a multiple of 16
-cudaError_t launch_tc_row_sweep(const Prob<float>& P, int wsel, int hsel, int dsel, int flags, bool bf16,
-                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
-cudaError_t launch_tc_col_sweep(const Prob<float>& P, int wsel, int hsel, int csel, int flags, bool bf16,
-                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+
+// Tensor maps over the shadow operand copies (built once per plan).
+struct TcMaps {
+  CUtensorMap wsA, wsB;      // sWS, boxes 32 x 128 and 32 x 32
+  CUtensorMap htA, htB;      // sHT, boxes 32 x 128 and 32 x 32
+  CUtensorMap hs, ch1, ch2;  // [kp][Np], box 32 x kp
+  CUtensorMap wt, cw1, cw2;  // [kp][Fp], box 32 x kp
+  bool ok = false;
+};
+bool tc_build_maps(const Prob<float>& P, TcMaps* m);
+
+cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int dsel, int flags,
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int csel, int flags,
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, int flags, const BetaParams& bp,
+                             double* lossPart, int* status, cudaStream_t st);
+cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, int flags, const BetaParams& bp,
+                             double* lossPart, int* status, cudaStream_t st);
 
 // Sparse beta = 1 path (sparse_kl.cu).
 struct SparseKL {

@@ -79,7 +79,7 @@ loss_noalloc_kernel(int64_t F, int64_t N, int K, const T* __restrict__ V, int64_
     if (f < F && n < N) {
       T vt = T(0);
       for (int k = 0; k < K; ++k) vt = fma(W[f * K + k], H[(int64_t)k * N + n], vt);
-      acc += (double)DB<T>::eval(V[f * ldv + n] + kappa, vt + kappa, bp.beta, bp.kind);
+      acc += (double)DB<T>::eval(V[f * ldv + n] + kappa, vt + kappa, bp, bp.kind);
     }
   }
   acc = block_sum(acc, red);
@@ -127,6 +127,7 @@ extern "C" nmf_status nmf_loss_noalloc(int64_t F, int64_t N, int32_t K, double b
   bp.gamma = gamma_of(beta);
   bp.kappa = kappa;
   bp.kind = beta_kind(beta);
+  fill_series(bp);
   if (precision == NMF_FP64)
     loss_noalloc_kernel<double><<<(unsigned)tiles, kThreads, 0, st>>>(
         F, N, K, static_cast<const double*>(V_dev), ldv, static_cast<const double*>(W_dev),

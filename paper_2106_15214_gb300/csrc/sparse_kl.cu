@@ -382,10 +382,8 @@ cudaError_t csc_pass_kj(const SparseKL& s, const float* Wd, const float* Hd, con
                         const float* den, float* Hout, double* lossPart, int* status, cudaStream_t st) {
   auto kern = csc_pass_kernel<KJ, COMPUTE, OUT>;
   const size_t sm = sizeof(float) * 3 * s.K * (CB + 1);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(kern), sm);
+  if (e != cudaSuccess) return e;
   const int grid = (int)((s.N + CB - 1) / CB);
   kern<<<grid, WPB * 32, sm, st>>>(s.colptr, s.cscRow, s.cscPos, s.val, s.a, Wd, Hd, Hbase, den, Hout, s.N, s.K,
                                    lossPart, status);

@@ -20,6 +20,8 @@
 // result is deterministic.
 #pragma once
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace nmf {
@@ -51,7 +53,7 @@ __device__ __forceinline__ T phase_a(const T* Ws, int KP, const T* Hs, int K,
       vt += kappa;
       const T v = V[gf * ldv + gn] + kappa;
       ab_terms<BK, T>(v, vt, bm2, a, b);
-      if (wantLoss) tl += (T)DB<T>::eval(v, vt, bp.beta, BK);
+      if (wantLoss) tl += (T)DB<T>::eval(v, vt, bp, BK);
     }
     As[f * TP + lane] = a;
     Bs[f * TP + lane] = b;
@@ -275,6 +277,11 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
     P.chiW1[idx] = c1;
     P.chiW2[idx] = c2;
+    if (tc && P.sCW1) {                       // transposed TF32 copies for the tensor-core sweeps
+      const int64_t f = idx / P.K, k = idx - f * P.K;
+      P.sCW1[k * P.Fp + f] = tf32_round(c1);
+      P.sCW2[k * P.Fp + f] = tf32_round(c2);
+    }
   }
 }
 
@@ -307,6 +314,11 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     chi_terms<BK, T>(x, P.Ht[idx], (T)bp.beta, c1, c2);
     P.chiH1[idx] = c1;
     P.chiH2[idx] = c2;
+    if (tc && P.sCH1) {
+      const int64_t k = idx / P.N, n = idx - k * P.N;
+      P.sCH1[k * P.Np + n] = tf32_round(c1);
+      P.sCH2[k * P.Np + n] = tf32_round(c2);
+    }
   }
 }
 
@@ -321,13 +333,29 @@ begin_iteration_kernel(const Prob<T>* __restrict__ probs, int count, const int* 
     const int pi = find_problem(prefW, count, b);
     const Prob<T> P = probs[pi];
     const int64_t idx = (int64_t)(b - prefW[pi]) * EW + threadIdx.x;
-    if (idx < P.F * P.K) P.Wt[idx] = P.W[idx];
+    if (idx < P.F * P.K) {
+      const T w = P.W[idx];
+      P.Wt[idx] = w;
+      if (P.sWS) {                         // TF32 shadows for the tensor-core sweeps
+        const int64_t f = idx / P.K, k = idx - f * P.K;
+        P.sWS[f * P.ks + k] = tf32_round(w);
+        P.sWT[k * P.Fp + f] = tf32_round(w);
+      }
+    }
   } else {
     b -= totW;
     const int pi = find_problem(prefH, count, b);
     const Prob<T> P = probs[pi];
     const int64_t idx = (int64_t)(b - prefH[pi]) * EW + threadIdx.x;
-    if (idx < (int64_t)P.K * P.N) P.Ht[idx] = P.H[idx];
+    if (idx < (int64_t)P.K * P.N) {
+      const T h = P.H[idx];
+      P.Ht[idx] = h;
+      if (P.sHT) {
+        const int64_t k = idx / P.N, n = idx - k * P.N;
+        P.sHT[n * P.ks + k] = tf32_round(h);
+        P.sHS[k * P.Np + n] = tf32_round(h);
+      }
+    }
   }
 }
 
@@ -377,6 +405,37 @@ normalize_apply_kernel(const Prob<T>* __restrict__ probs, int count, const int* 
   }
 }
 
+// Shadows of the current W (which & 1) and / or H (which & 2), TF32-rounded,
+// in the layouts the tensor-core sweeps load by TMA (single problem).
+template <typename T>
+__global__ void __launch_bounds__(EW)
+shadow_factors_kernel(Prob<T> P, int which, const int* __restrict__ status) {
+  if (*status) return;
+  const int64_t FK = P.F * P.K, KN = (int64_t)P.K * P.N;
+  const int64_t lo = (which & 1) ? 0 : FK, hi = (which & 2) ? FK + KN : FK;
+  for (int64_t i = lo + (int64_t)blockIdx.x * EW + threadIdx.x; i < hi; i += (int64_t)gridDim.x * EW) {
+    if (i < FK) {
+      const int64_t f = i / P.K, k = i - f * P.K;
+      const T w = tf32_round(P.W[i]);
+      P.sWS[f * P.ks + k] = w;
+      P.sWT[k * P.Fp + f] = w;
+    } else {
+      const int64_t j = i - FK, k = j / P.N, n = j - k * P.N;
+      const T h = tf32_round(P.H[j]);
+      P.sHT[n * P.ks + k] = h;
+      P.sHS[k * P.Np + n] = h;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_shadow_factors(const Prob<T>& P, int which, const int* status, cudaStream_t st) {
+  const int64_t n = ((which & 1) ? P.F * P.K : 0) + ((which & 2) ? (int64_t)P.K * P.N : 0);
+  const unsigned grid = (unsigned)std::min<int64_t>(2048, (n + EW - 1) / EW);
+  shadow_factors_kernel<T><<<grid > 0 ? grid : 1, EW, 0, st>>>(P, which, status);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(EW)
 kkt_kernel(const T* __restrict__ W, const T* __restrict__ gW, int64_t nW, const T* __restrict__ H,
@@ -406,8 +465,7 @@ inline size_t col_smem_bytes(int K, int csel) {
 
 template <typename KernelT>
 inline cudaError_t prep_smem(KernelT kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return ensure_smem_attr(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <typename T, int BK, int KJ>
@@ -538,6 +596,7 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \
-                                     double*, cudaStream_t);
+                                     double*, cudaStream_t);                                       \
+  template cudaError_t launch_shadow_factors<T>(const Prob<T>&, int, const int*, cudaStream_t);
 
 }  // namespace nmf

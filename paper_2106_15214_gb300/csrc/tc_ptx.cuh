@@ -120,6 +120,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint64_t
   return true;
 }
 
+// ---- asynchronous copies ------------------------------------------------------
+// 4-byte cp.async global -> shared; src_bytes = 0 writes zeros (src must still
+// be a valid address).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+               :: "r"(smem_u32(smem_dst)), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+// Arrives on the mbarrier once all of this thread's earlier cp.async copies have
+// landed; counts as one of the barrier's expected arrivals (.noinc).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* m) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               :: "r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// 2-D TMA tile load (x = inner coordinate in elements, y = row); completes
+// `bytes` of transaction count on the mbarrier. x * element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(smem_u32(smem_dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(m)) : "memory");
+}
+
 // ---- TMEM loads -------------------------------------------------------------
 // Each thread of the warp reads 32 consecutive 32-bit columns of its lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* r) {
@@ -146,6 +174,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* r) {
       : "r"(taddr));
   #pragma unroll
   for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(v[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* r) {
+  uint32_t v[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(taddr));
+  #pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = __uint_as_float(v[i]);
 }
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

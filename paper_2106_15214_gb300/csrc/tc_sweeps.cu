@@ -188,7 +188,7 @@ tc_row_sweep_kernel(Prob<float> P, int wsel, int hsel, int dsel, int flags, Beta
           if (valid) {
             const float v = vv[j] + kappa, y = vt[4 * c + j] + kappa;
             ab_terms<BK, float>(v, y, bm2, a[j], b[j]);
-            if (wantLoss) tl += (float)DB<float>::eval(v, y, bp.beta, BK);
+            if (wantLoss) tl += (float)DB<float>::eval(v, y, bp, BK);
           }
         }
         *reinterpret_cast<float4*>(As + off) = make_float4(to_tf32(a[0]), to_tf32(a[1]), to_tf32(a[2]), to_tf32(a[3]));
@@ -355,7 +355,7 @@ tc_col_sweep_kernel(Prob<float> P, int wsel, int hsel, int csel, int flags, Beta
             const float v = reinterpret_cast<const float*>(Vs)[f * MT + ncol] + kappa;
             const float y = vt[4 * c + j] + kappa;
             ab_terms<BK, float>(v, y, bm2, a[j], b[j]);
-            if (wantLoss) tl += (float)DB<float>::eval(v, y, bp.beta, BK);
+            if (wantLoss) tl += (float)DB<float>::eval(v, y, bp, BK);
           }
         }
         const uint32_t off = sw128_offset(ncol, 4 * fb);
@@ -410,7 +410,7 @@ tc_col_sweep_kernel(Prob<float> P, int wsel, int hsel, int csel, int flags, Beta
 
 template <typename Kern>
 cudaError_t prep(Kern k, size_t sm) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return ensure_smem_attr(reinterpret_cast<const void*>(k), sm);
 }
 
 }  // namespace
@@ -431,21 +431,23 @@ int tc_kp(int K) { return (K + 15) & ~15; }
     return cudaGetLastError();                                                                    \
   } while (0)
 
-cudaError_t launch_tc_row_sweep(const Prob<float>& P, int wsel, int hsel, int dsel, int flags, bool bf16,
-                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
+cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int dsel, int flags,
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
   (void)bf16;
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
+  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_row(P, *maps, dsel, flags, bp, lossPart, status, st);
   const size_t sm = row_smem(kp);
   const unsigned grid = (unsigned)(P.tcRowTiles * P.tcS);
   NMF_TC_BK_DISPATCH(tc_row_sweep_kernel, grid, sm, P, wsel, hsel, dsel, flags, bp, lossPart, status);
 }
 
-cudaError_t launch_tc_col_sweep(const Prob<float>& P, int wsel, int hsel, int csel, int flags, bool bf16,
-                                const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
+cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int csel, int flags,
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
   (void)bf16;
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
+  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_col(P, *maps, csel, flags, bp, lossPart, status, st);
   const size_t sm = col_smem(kp);
   const unsigned grid = (unsigned)(P.tcColTiles * P.tcR);
   NMF_TC_BK_DISPATCH(tc_col_sweep_kernel, grid, sm, P, wsel, hsel, csel, flags, bp, lossPart, status);
