@@ -103,7 +103,11 @@ nmf_status nmf_set_options(nmf_ctx* ctx, nmf_precision precision, nmf_order orde
  * Algorithm 1) per outer iteration. */
 nmf_status nmf_set_subiterations(nmf_ctx* ctx, int32_t L);
 
-/* Borrows dense V (device, F x N row-major, leading dimension ldv >= N). */
+/* Borrows dense V (device, F x N row-major, leading dimension ldv >= N).
+ * NMF_TF32 / NMF_BF16 contexts whose rows of V are not 16-byte aligned
+ * (ldv * 4 not a multiple of 16, or V not 16-byte aligned) read V through a
+ * row-padded device copy taken at the first step after this call: call
+ * nmf_set_dense again after changing the contents of V. */
 nmf_status nmf_set_dense(nmf_ctx* ctx, const void* V_dev, int64_t ldv);
 
 /* Borrows sparse V in CSR form (device arrays): rowptr has F + 1 entries,

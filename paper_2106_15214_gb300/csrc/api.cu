@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -72,6 +73,12 @@ struct nmf_ctx {
   SparseKL sp;
   Timer timer;
   TcMaps tcmaps;
+  double* d_normPart = nullptr;   // fused normalisation: [W epilogue blocks][K]
+  unsigned* d_counter = nullptr;  // completion counter of the fused epilogues
+  bool lossFused = false;
+  void* Vpad = nullptr;           // row-padded copy of V (tensor-core contexts, unaligned rows)
+  const void* vpadSrc = nullptr;
+  bool vDirty = true;
   // CUDA graphs of step calls (see capture_step)
   struct GraphEntry {
     uint64_t key = 0;
@@ -186,16 +193,47 @@ int64_t best_split(int64_t fixedTiles, int64_t streamTiles, int sms) {
   return best;
 }
 
+// Tiling of one tensor-core sweep: `fixedTiles` 128-wide tiles, `streamLen`
+// streamed indices (32 per tile step). NMF_TC_CLUSTER=<c> (2, 4 or 8) makes
+// the blocks of one tile form clusters of c whose partial sums are added
+// through distributed shared memory, so the sweep writes split / c slices
+// (the split sized for the blocks resident in clusters of c). Off by default:
+// on the 361 x 2429 and 513 x 20000 workloads the tree and the cluster
+// scheduling cost the sweep more than the shorter slice sums save.
+void tc_split(int64_t fixedTiles, int64_t streamLen, int kp, int sms, int64_t& chunk, int& split, int& cluster,
+              int& slices) {
+  const int64_t streamTiles = cdiv(streamLen, 32);
+  const char* env = std::getenv("NMF_TC_CLUSTER");
+  const int forced = env ? std::atoi(env) : 0;
+  cluster = 1;
+  int64_t S = best_split(fixedTiles, streamTiles, sms);
+  if (kp <= 64 && (forced == 2 || forced == 4 || forced == 8)) {
+    const int cap = tc_ws_capacity(kp, forced);
+    if (cap >= forced) {
+      cluster = forced;
+      S = best_split(fixedTiles, streamTiles, cap);
+    }
+  }
+  chunk = cdiv(streamTiles, S) * 32;
+  const int64_t sp = cdiv(streamLen, chunk);
+  split = (int)(cdiv(sp, cluster) * cluster);
+  slices = split / cluster;
+}
+
 void tc_tiling(Prob<float>& P, int sms) {
-  const int64_t nT = cdiv(P.N, 32), fT = cdiv(P.F, 32);
+  const int kp = (P.K + 15) & ~15;
   P.tcRowTiles = (int)cdiv(P.F, 128);
-  const int64_t S = best_split(P.tcRowTiles, nT, sms);
-  P.tcChunkN = cdiv(nT, S) * 32;
-  P.tcS = (int)cdiv(P.N, P.tcChunkN);
+  tc_split(P.tcRowTiles, P.N, kp, sms, P.tcChunkN, P.tcSplitS, P.tcClusterS, P.tcS);
   P.tcColTiles = (int)cdiv(P.N, 128);
-  const int64_t R = best_split(P.tcColTiles, fT, sms);
-  P.tcChunkF = cdiv(fT, R) * 32;
-  P.tcR = (int)cdiv(P.F, P.tcChunkF);
+  tc_split(P.tcColTiles, P.F, kp, sms, P.tcChunkF, P.tcSplitR, P.tcClusterR, P.tcR);
+  if (std::getenv("NMF_TC_DEBUG"))
+    std::fprintf(stderr, "nmf tc capacity (blocks resident) cluster 1/2/4/8: %d %d %d %d (sms %d)\n",
+                 tc_ws_capacity(kp, 1), tc_ws_capacity(kp, 2), tc_ws_capacity(kp, 4), tc_ws_capacity(kp, 8), sms);
+  if (std::getenv("NMF_TC_DEBUG"))
+    std::fprintf(stderr, "nmf tc tiling F=%lld N=%lld K=%d: row %d tiles x %d blocks (cluster %d, %d slices, chunk %lld); "
+                 "col %d tiles x %d blocks (cluster %d, %d slices, chunk %lld)\n",
+                 (long long)P.F, (long long)P.N, P.K, P.tcRowTiles, P.tcSplitS, P.tcClusterS, P.tcS,
+                 (long long)P.tcChunkN, P.tcColTiles, P.tcSplitR, P.tcClusterR, P.tcR, (long long)P.tcChunkF);
 }
 template <typename T> void tc_tiling(Prob<T>&, int) {}
 
@@ -218,6 +256,8 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     tl[i] = tiling(F, N, c->sms, c->batched);
     probs[i].F = F; probs[i].N = N; probs[i].K = K;
     probs[i].tcS = probs[i].tcR = 1;
+    probs[i].tcSplitS = probs[i].tcSplitR = 1;
+    probs[i].tcClusterS = probs[i].tcClusterR = 1;
     if (!c->batched) tc_tiling(probs[i], c->sms);
     const int Smax = std::max(tl[i].S, probs[i].tcS), Rmax = std::max(tl[i].R, probs[i].tcR);
     const size_t FK = (size_t)F * K, KN = (size_t)K * N;
@@ -295,10 +335,12 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   all.insert(all.end(), pw.begin(), pw.end());
   all.insert(all.end(), ph.begin(), ph.end());
   all.insert(all.end(), pk.begin(), pk.end());
-  const int tcRowGrid = probs[0].tcRowTiles * probs[0].tcS, tcColGrid = probs[0].tcColTiles * probs[0].tcR;
+  const int tcRowGrid = probs[0].tcRowTiles * probs[0].tcSplitS, tcColGrid = probs[0].tcColTiles * probs[0].tcSplitR;
   all.insert(all.end(), {0, c->batched ? 0 : tcRowGrid, 0, c->batched ? 0 : tcColGrid});
   NMF_CU(cudaMemcpy(tabs, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
   pl.d_prefTc = tabs + 5 * (cnt + 1);
+  pl.rowSlices[0] = probs[0].S;
+  pl.rowSlices[1] = probs[0].tcS;
   pl.d_prefRow = tabs; pl.totRow = pr[cnt];
   pl.d_prefCol = tabs + (cnt + 1); pl.totCol = pc[cnt];
   pl.d_prefW = tabs + 2 * (cnt + 1); pl.totW = pw[cnt];
@@ -307,6 +349,12 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
   if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max(tcRowGrid, tcColGrid));
   NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
+  if (!c->batched) {
+    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_normPart),
+                   sizeof(double) * (size_t)rows_epilogue_grid(pl.totW, ROWS_EPI_MAX_LANES) * c->K[0]));
+    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_counter), 256));
+    NMF_CU(cudaMemset(c->d_counter, 0, 256));
+  }
   return NMF_OK;
 }
 
@@ -325,6 +373,22 @@ nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
       P.W = static_cast<T*>(c->W);
       P.H = static_cast<T*>(c->H);
       P.ldv = c->ldv;
+      // Tensor-core sweeps stream V by TMA, which needs 16-byte aligned rows:
+      // otherwise keep a row-padded copy, taken when V is set.
+      const bool tcPrec = c->prec == NMF_TF32 || c->prec == NMF_BF16;
+      if (tcPrec && sizeof(T) == 4 &&
+          (((c->ldv * 4) & 15) != 0 || (reinterpret_cast<uintptr_t>(c->V) & 15u) != 0)) {
+        const int64_t Np = (P.N + 3) & ~int64_t(3);
+        if (!c->Vpad) NMF_TRY(dalloc(c, &c->Vpad, sizeof(T) * (size_t)P.F * Np));
+        if (c->vDirty || c->vpadSrc != c->V) {
+          NMF_CU(cudaMemcpy2DAsync(c->Vpad, sizeof(T) * Np, c->V, sizeof(T) * c->ldv, sizeof(T) * P.N, P.F,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+          c->vpadSrc = c->V;
+          c->vDirty = false;
+        }
+        P.V = static_cast<const T*>(c->Vpad);
+        P.ldv = Np;
+      }
     }
     oW += (size_t)P.F * P.K; oH += (size_t)P.K * P.N; oV += (size_t)P.F * P.N;
   }
@@ -443,35 +507,63 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     }
     return NMF_OK;
   };
-  auto rows_epi = [&](int basesel, int chi) -> nmf_status {
+  // single problems fold the objective's finalisation and the normalisation
+  // into the epilogues (EpiFuse); batched contexts use the separate kernels
+  const bool fuse = !c->batched;
+  const int rowGrid = tc ? c->hpf[0].tcRowTiles * c->hpf[0].tcSplitS : pl.totRow;
+  const int colGrid = tc ? c->hpf[0].tcColTiles * c->hpf[0].tcSplitR : pl.totCol;
+  auto fz_for = [&](int flags, bool lossFromRow) {
+    EpiFuse f;
+    if (!fuse) return f;
+    f.flags = flags;
+    f.lossPart = lp;
+    f.lossBlocks = lossFromRow ? rowGrid : colGrid;
+    f.lossOut = c->d_lossOut;
+    f.normPart = c->d_normPart;
+    f.counter = c->d_counter;
+    return f;
+  };
+  auto rows_epi = [&](int basesel, int chi, int flags) -> nmf_status {
+    const EpiFuse f = fz_for(flags, true);
     NMF_TRY(cu(timed(&c->timer, st, "rows_epilogue", 1, [&] {
-      return launch_rows_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
+      return launch_rows_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci, f);
     })));
     return basesel == SEL_CUR ? shadows(1) : NMF_OK;   // alternating: the new W feeds the next sweep
   };
-  auto cols_epi = [&](int basesel, int chi) -> nmf_status {
+  auto cols_epi = [&](int basesel, int chi, int flags) -> nmf_status {
+    const EpiFuse f = fz_for(flags, false);
     NMF_TRY(cu(timed(&c->timer, st, "cols_epilogue", 1, [&] {
-      return launch_cols_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci);
+      return launch_cols_epilogue<T>(pl, EPI_UPDATE, basesel, chi, bp, nullptr, status, st, tci, f);
     })));
     return basesel == SEL_CUR ? shadows(2) : NMF_OK;
   };
+  const bool norm = c->normalize != 0;
   for (int it = 0; it < iters; ++it) {
     const bool lossHere = wantLoss && it == iters - 1;
     const int CL = C | (lossHere ? SWEEP_LOSS : 0);
+    const int lossFlag = (fuse && lossHere) ? FUSE_LOSS : 0;
     NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
+    bool normDone = false;
     if (joint) {
       for (int l = 1; l <= L; ++l) {
         const int f1 = l == 1 ? CL : C;
+        const int lf = l == 1 ? lossFlag : 0;
+        const bool lastL = l == L;
         if (wfirst) {
           NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1));
-          NMF_TRY(rows_epi(SEL_TILDE, 1));
+          NMF_TRY(rows_epi(SEL_TILDE, 1, lf | ((fuse && norm && lastL) ? FUSE_NORM_PART : 0)));
           NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C));
-          NMF_TRY(cols_epi(SEL_TILDE, l < L));
+          NMF_TRY(cols_epi(SEL_TILDE, l < L, (fuse && norm && lastL) ? FUSE_NORM_APPLY : 0));
+          normDone = normDone || (fuse && norm && lastL);
         } else {
           NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, l == 1 ? OP_SELF : OP_CHI, f1));
-          NMF_TRY(cols_epi(SEL_TILDE, 1));
+          NMF_TRY(cols_epi(SEL_TILDE, 1, lf));
           NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C));
-          NMF_TRY(rows_epi(SEL_TILDE, l < L));
+          NMF_TRY(rows_epi(SEL_TILDE, l < L, (fuse && norm && lastL) ? FUSE_NORM_PART : 0));
+          if (fuse && norm && lastL) {
+            NMF_CU(timed(&c->timer, st, "normalize", 1, [&] { return launch_normalize_apply<T>(pl, status, st); }));
+            normDone = true;
+          }
         }
       }
     } else {
@@ -479,18 +571,28 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         const bool doW = (half == 0) == wfirst;
         for (int l = 1; l <= L; ++l) {
           const int fl = (half == 0 && l == 1) ? CL : C;
+          const int lf = (half == 0 && l == 1) ? lossFlag : 0;
+          const bool lastUpdate = half == 1 && l == L;    // the iteration's last update
           if (doW) {
             NMF_TRY(row_sweep(SEL_CUR, SEL_CUR, OP_SELF, fl));
-            NMF_TRY(rows_epi(SEL_CUR, 0));
+            // norms of the final W: W's last update (W first: end of half 0; H first: the last update)
+            const bool finalW = l == L;
+            NMF_TRY(rows_epi(SEL_CUR, 0, lf | ((fuse && norm && finalW) ? FUSE_NORM_PART : 0)));
+            if (lastUpdate && fuse && norm) {
+              NMF_CU(timed(&c->timer, st, "normalize", 1, [&] { return launch_normalize_apply<T>(pl, status, st); }));
+              normDone = true;
+            }
           } else {
             NMF_TRY(col_sweep(SEL_CUR, SEL_CUR, OP_SELF, fl));
-            NMF_TRY(cols_epi(SEL_CUR, 0));
+            NMF_TRY(cols_epi(SEL_CUR, 0, lf | ((fuse && norm && lastUpdate) ? FUSE_NORM_APPLY : 0)));
+            normDone = normDone || (fuse && norm && lastUpdate);
           }
         }
       }
     }
-    if (c->normalize) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
+    if (norm && !normDone) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
   }
+  c->lossFused = fuse;
   if (wantLoss) c->lossPrefix = (wfirst ? 0 : 1) + (tc ? 2 : 0);
   return NMF_OK;
 }
@@ -580,7 +682,7 @@ nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss) {
     const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
     if (c->prec == NMF_FP64) NMF_TRY(run_dense<double>(c, c->pd, joint, iters, wantLoss, false));
     else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss, tc));
-    if (wantLoss) NMF_TRY(finalize_loss_dense(c));
+    if (wantLoss && !c->lossFused) NMF_TRY(finalize_loss_dense(c));
   }
   return enqueue_readback(c, wantLoss);
 }
@@ -698,6 +800,11 @@ bool valid_beta(double b) { return std::isfinite(b); }
 // Loss finalisation kernel: per problem, fixed-order sum of its block partials.
 // ---------------------------------------------------------------------------
 namespace nmf {
+int rows_epilogue_lanes_host(int count, int slices) {
+  if (count != 1) return 1;
+  return slices >= 16 ? 8 : slices >= 8 ? 4 : slices >= 4 ? 2 : 1;
+}
+
 __global__ void loss_finalize_kernel(const int* __restrict__ prefix, const double* __restrict__ part,
                                      double* __restrict__ out) {
   __shared__ double red[32];
@@ -793,6 +900,7 @@ nmf_status nmf_set_dense(nmf_ctx* c, const void* V_dev, int64_t ldv) {
   c->V = V_dev;
   c->ldv = ldv;
   c->tableDirty = true;
+  c->vDirty = true;
   return NMF_OK;
 }
 
@@ -971,10 +1079,21 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
     if (s != NMF_OK) return s;
   }
   const void* keepV = c->V; void* keepW = c->W; void* keepH = c->H; int64_t keepLd = c->ldv;
-  NMF_CU(cudaMemcpyAsync(c->stageV, V_host, es * c->elemsV, cudaMemcpyHostToDevice, c->stream));
+  const int64_t F = c->F[0], N = c->N[0];
+  const bool tcPrec = c->prec == NMF_TF32 || c->prec == NMF_BF16;
+  if (tcPrec && ((N * 4) & 15) != 0) {
+    // rows of V are not 16-byte aligned: copy straight into the padded layout the tensor-core sweeps read
+    const int64_t Np = (N + 3) & ~int64_t(3);
+    if (!c->Vpad) NMF_TRY(dalloc(c, &c->Vpad, es * (size_t)F * Np));
+    NMF_CU(cudaMemcpy2DAsync(c->Vpad, es * Np, V_host, es * N, es * N, F, cudaMemcpyHostToDevice, c->stream));
+    c->V = c->Vpad; c->ldv = Np;
+  } else {
+    NMF_CU(cudaMemcpyAsync(c->stageV, V_host, es * c->elemsV, cudaMemcpyHostToDevice, c->stream));
+    c->V = c->stageV; c->ldv = N;
+  }
   NMF_CU(cudaMemcpyAsync(c->stageW, W_host, es * c->elemsW, cudaMemcpyHostToDevice, c->stream));
   NMF_CU(cudaMemcpyAsync(c->stageH, H_host, es * c->elemsH, cudaMemcpyHostToDevice, c->stream));
-  c->V = c->stageV; c->W = c->stageW; c->H = c->stageH; c->ldv = c->N[0];
+  c->W = c->stageW; c->H = c->stageH;
   c->tableDirty = true;
   nmf_status s = step(c, true, iters, loss_out);
   if (s == NMF_OK || s == NMF_ENONFINITE) {
@@ -985,6 +1104,7 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
   }
   c->V = keepV; c->W = keepW; c->H = keepH; c->ldv = keepLd;
   c->tableDirty = true;
+  c->vDirty = true;
   return s;
 }
 

@@ -75,9 +75,13 @@ struct Prob {
   int64_t chunkF;    // rows per column-sweep chunk (multiple of BF)
   // tensor-core sweeps (single problems): 128-row / 128-column MMA tiles
   int tcRowTiles;    // ceil(F / 128)
-  int tcS;           // column chunks of the tensor-core row sweep
+  int tcS;           // partial slices the tensor-core row sweep writes (blocks / cluster size)
   int tcColTiles;    // ceil(N / 128)
-  int tcR;           // row chunks of the tensor-core column sweep
+  int tcR;           // partial slices the tensor-core column sweep writes
+  int tcSplitS;      // blocks along N per row tile (padded to a multiple of tcClusterS)
+  int tcClusterS;    // blocks of one cluster, combined through distributed shared memory
+  int tcSplitR;      // blocks along F per column tile (padded to a multiple of tcClusterR)
+  int tcClusterR;
   int64_t tcChunkN;  // multiple of 32
   int64_t tcChunkF;  // multiple of 32
   // TF32-rounded, zero-padded operand copies read by TMA in the tensor-core

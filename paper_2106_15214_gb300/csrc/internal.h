@@ -130,6 +130,7 @@ struct Plan {
   int* d_prefH = nullptr; int totH = 0;       // EW-entry blocks over K x N
   int* d_prefK = nullptr; int totK = 0;       // one block per column of W
   int* d_prefTc = nullptr;                    // {0, tc row grid, 0, tc column grid} (single problem)
+  int rowSlices[2] = {1, 1};                  // row-sweep partial slices: SIMT, tensor core (single problem)
 };
 
 template <typename T>
@@ -142,15 +143,43 @@ cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, in
                              cudaStream_t st);
 // W epilogue: W = base . (sum num / sum den)^gamma (mode EPI_UPDATE, base = W or Wt,
 // chi computed from (W_new, Wt) when want_chi) or gout = sum den - sum num (EPI_GRAD).
+// Optional work fused into the epilogues (single problems only; flags 0 = none):
+// FUSE_LOSS: the last block sums the preceding sweep's loss partials into lossOut;
+// FUSE_NORM_PART (W epilogue): per-block sums of squares of the new W, turned into
+// the column norms (Prob::norms) by the last block; FUSE_NORM_APPLY (H epilogue):
+// H rows *= norms and W columns /= norms (normalisation, Sec. 4.1.2).
+enum { FUSE_LOSS = 1, FUSE_NORM_PART = 2, FUSE_NORM_APPLY = 4 };
+struct EpiFuse {
+  int flags = 0;
+  const double* lossPart = nullptr;
+  int lossBlocks = 0;
+  double* lossOut = nullptr;
+  double* normPart = nullptr;   // [W epilogue blocks][K]
+  unsigned* counter = nullptr;  // zero between launches
+};
+
 // tc != 0: the partials come from the tensor-core sweeps (tcS / tcR slices).
 template <typename T>
 cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
                                  const BetaParams& bp, T* gout, int* status, cudaStream_t st,
-                                 int tc = 0);
+                                 int tc = 0, const EpiFuse& fz = EpiFuse());
 template <typename T>
 cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
                                  const BetaParams& bp, T* gout, int* status, cudaStream_t st,
-                                 int tc = 0);
+                                 int tc = 0, const EpiFuse& fz = EpiFuse());
+template <typename T>
+cudaError_t launch_normalize_apply(const Plan<T>& pl, const int* status, cudaStream_t st);
+// Lanes per entry of the W epilogue: for a single problem 8, 4 or 2 with
+// >= 16, >= 8 or >= 4 partial slices, else 1. A single problem runs blocks of
+// 1024 threads (1024 / G entries each), a batched context blocks of EW.
+constexpr int ROWS_EPI_MAX_LANES = 8;
+int rows_epilogue_lanes_host(int count, int slices);
+// blocks of the single-problem W epilogue; totW blocks of EW entries cover F x K
+inline int rows_epilogue_grid(int totW, int G) { return (int)(((int64_t)totW * EW * G + 1023) / 1024); }
+template <typename T>
+inline int rows_epilogue_lanes(const Plan<T>& pl, int tc) {
+  return pl.count == 1 ? rows_epilogue_lanes_host(1, pl.rowSlices[tc ? 1 : 0]) : 1;
+}
 // Copies W -> Wt and H -> Ht for every problem (skipped once status is set).
 template <typename T>
 cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st);
@@ -189,6 +218,9 @@ cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int ws
                                 bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
 cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int csel, int flags,
                                 bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+// Blocks of the warp-specialised sweep (padded rank kp) that can be resident
+// at once when launched in clusters of `csize`; 0 when it cannot launch.
+int tc_ws_capacity(int kp, int csize);
 cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, int flags, const BetaParams& bp,
                              double* lossPart, int* status, cudaStream_t st);
 cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, int flags, const BetaParams& bp,

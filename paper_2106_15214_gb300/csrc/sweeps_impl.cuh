@@ -248,78 +248,224 @@ col_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __rest
   }
 }
 
-// W-half epilogue over F x K entries.
-template <typename T, int BK>
-__global__ void __launch_bounds__(EW)
-rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
-                     int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
-                     int* __restrict__ status, int tc) {
-  if (*status) return;
-  const int b = blockIdx.x;
-  const int pi = find_problem(prefix, count, b);
-  const Prob<T> P = probs[pi];
-  const int64_t FK = P.F * P.K;
-  const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
-  if (idx >= FK) return;
-  T num = T(0), den = T(0);
-  const int slices = tc ? P.tcS : P.S;
-  for (int s = 0; s < slices; ++s) {
-    num += P.rowPart[(int64_t)s * 2 * FK + idx];
-    den += P.rowPart[(int64_t)s * 2 * FK + FK + idx];
-  }
-  if (mode == EPI_GRAD) { gout[idx] = den - num; return; }
-  const T base = basesel == SEL_TILDE ? P.Wt[idx] : P.W[idx];
-  const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
-  if (!isfinite(x)) atomicExch(status, 4);
-  P.W[idx] = x;
-  if (want_chi) {
-    T c1, c2;
-    chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
-    P.chiW1[idx] = c1;
-    P.chiW2[idx] = c2;
-    if (tc && P.sCW1) {                       // transposed TF32 copies for the tensor-core sweeps
-      const int64_t f = idx / P.K, k = idx - f * P.K;
-      P.sCW1[k * P.Fp + f] = tf32_round(c1);
-      P.sCW2[k * P.Fp + f] = tf32_round(c2);
+// Fixed-order sum of `slices` partial slices at stride `stride`, loads in
+// flight together (8 at a time), additions in slice order.
+template <typename T>
+__device__ __forceinline__ void sum_slices(const T* __restrict__ part, int64_t stride, int64_t half, int slices,
+                                           T& num, T& den) {
+  num = T(0);
+  den = T(0);
+  int s = 0;
+  for (; s + 8 <= slices; s += 8) {
+    T a[8], b[8];
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = part[(int64_t)(s + j) * stride];
+      b[j] = part[(int64_t)(s + j) * stride + half];
     }
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) { num += a[j]; den += b[j]; }
+  }
+  for (; s < slices; ++s) {
+    num += part[(int64_t)s * stride];
+    den += part[(int64_t)s * stride + half];
   }
 }
 
-// H-half epilogue over K x N entries.
+// The last block to finish (after every block published its partials) does
+// the fixed-order finalisations: column norms of W from the per-block partial
+// sums of squares, and / or the objective from the sweep's loss partials.
+template <typename T>
+__device__ __forceinline__ void last_block_finalize(const EpiFuse& fz, const Prob<T>& P, int nblocks,
+                                                    double* sbuf /* blockDim.x doubles, for FUSE_NORM_PART */) {
+  __shared__ bool s_last;
+  __shared__ double red[32];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(fz.counter, 1u) == (unsigned)nblocks - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (fz.flags & FUSE_NORM_PART) {
+    // R threads per column: thread (k, j) sums the partials of blocks j, j + R,
+    // ... with eight loads in flight, then thread k adds its R sums in order
+    // (deterministic; one L2 round trip covers 8 R blocks).
+    const int t = threadIdx.x, R = blockDim.x / P.K;
+    double sq = 0.0;
+    if (t < R * P.K) {
+      const int k = t / R, j = t - k * R;
+      for (int b0 = j; b0 < nblocks; b0 += 8 * R) {
+        double v[8];
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int bb = b0 + u * R;
+          v[u] = bb < nblocks ? __ldcg(&fz.normPart[(int64_t)bb * P.K + k]) : 0.0;
+        }
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) sq += v[u];
+      }
+    }
+    sbuf[t] = sq;
+    __syncthreads();
+    if (t < P.K) {
+      double sum = 0.0;
+      for (int j = 0; j < R; ++j) sum += sbuf[t * R + j];
+      P.norms[t] = (T)sqrt(sum);
+    }
+  }
+  if (fz.flags & FUSE_LOSS) {
+    double sl = 0.0;
+    for (int b = threadIdx.x; b < fz.lossBlocks; b += blockDim.x) sl += __ldcg(&fz.lossPart[b]);
+    sl = block_sum(sl, red);
+    if (threadIdx.x == 0) fz.lossOut[0] = sl;
+  }
+  if (threadIdx.x == 0) *fz.counter = 0u;
+}
+
+// W-half epilogue over F x K entries. With fusion flags (single problem):
+// FUSE_NORM_PART also publishes this block's sums of squares of the new W per
+// column (the last block turns them into the column norms), FUSE_LOSS
+// finalises the objective of the preceding sweep.
+// NTH threads per block: 256 for batched contexts (blocks follow the prefix
+// table), 1024 for a single problem (fewer blocks, so fewer norm partials).
+template <typename T, int BK, int NTH>
+__global__ void __launch_bounds__(NTH)
+rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
+                     int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
+                     int* __restrict__ status, int tc, EpiFuse fz, int G) {
+  // With fusion every block must reach the completion counter, so a set status
+  // word only skips the arithmetic.
+  const bool skip = *status != 0;
+  if (skip && !fz.flags) return;
+  __shared__ double s_sq[NTH];
+  // G lanes per entry (single problem): lane j sums slices j, j + G, ... and a
+  // fixed butterfly combines them; G = 1 for batched contexts.
+  const int epb = NTH / G;                                 // entries per block
+  const int b = blockIdx.x;
+  const int pi = count == 1 ? 0 : find_problem(prefix, count, b);
+  const Prob<T> P = probs[pi];
+  const int64_t FK = P.F * P.K;
+  const int sub = threadIdx.x % G;
+  const int64_t idx = (int64_t)(b - (count == 1 ? 0 : prefix[pi])) * epb + threadIdx.x / G;
+  const bool inside = idx < FK && !skip;
+  const int slices = tc ? P.tcS : P.S;
+  T num = T(0), den = T(0);
+  if (inside) {
+    const T* part = P.rowPart + idx;
+    for (int s0 = sub; s0 < slices; s0 += 8 * G) {        // eight slices' loads in flight, added in slice order
+      T vn[8], vd[8];
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int sl = s0 + u * G;
+        vn[u] = sl < slices ? part[(int64_t)sl * 2 * FK] : T(0);
+        vd[u] = sl < slices ? part[(int64_t)sl * 2 * FK + FK] : T(0);
+      }
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        num += vn[u];
+        den += vd[u];
+      }
+    }
+  }
+  for (int o = 1; o < G; o <<= 1) {                        // G in {1, 2, 4, 8}: lanes of an entry share a warp
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  double sq = 0.0;
+  if (inside && sub == 0) {
+    if (mode == EPI_GRAD) {
+      gout[idx] = den - num;
+    } else {
+      const T base = basesel == SEL_TILDE ? P.Wt[idx] : P.W[idx];
+      const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+      if (!isfinite(x)) atomicExch(status, 4);
+      P.W[idx] = x;
+      sq = (double)x * (double)x;
+      if (want_chi) {
+        T c1, c2;
+        chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
+        P.chiW1[idx] = c1;
+        P.chiW2[idx] = c2;
+        if (tc && P.sCW1) {                       // transposed TF32 copies for the tensor-core sweeps
+          const int64_t f = idx / P.K, k = idx - f * P.K;
+          P.sCW1[k * P.Fp + f] = tf32_round(c1);
+          P.sCW2[k * P.Fp + f] = tf32_round(c2);
+        }
+      }
+    }
+  }
+  if (!fz.flags) return;
+  if (fz.flags & FUSE_NORM_PART) {
+    s_sq[threadIdx.x] = sq;
+    __syncthreads();
+    const int64_t first = (int64_t)b * epb;
+    for (int k = threadIdx.x; k < P.K; k += NTH) {
+      // entries of column k inside this block, summed in index order
+      int i = (int)(((int64_t)k - first % P.K + P.K) % P.K);
+      double acc = 0.0;
+      for (; i < epb && first + i < FK; i += P.K) acc += s_sq[i * G];
+      fz.normPart[(int64_t)b * P.K + k] = acc;
+    }
+  }
+  last_block_finalize<T>(fz, P, gridDim.x, s_sq);
+}
+
+// H-half epilogue over K x N entries. FUSE_LOSS finalises the objective of
+// the preceding sweep; FUSE_NORM_APPLY (the iteration's last kernel) scales
+// the new H rows by the column norms of W and, in extra blocks
+// [totH, totH + totW), divides W's columns by them (Sec. 4.1.2).
 template <typename T, int BK>
 __global__ void __launch_bounds__(EW)
 cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
-                     int* __restrict__ status, int tc) {
-  if (*status) return;
+                     int* __restrict__ status, int tc, EpiFuse fz, int totH) {
+  const bool skip = *status != 0;
+  if (skip && !(fz.flags & FUSE_LOSS)) return;
   const int b = blockIdx.x;
+  if ((fz.flags & FUSE_NORM_APPLY) && b >= totH) {      // W /= norms (single problem)
+    const Prob<T> P = probs[0];
+    const int64_t idx = (int64_t)(b - totH) * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const T nk = P.norms[idx % P.K];
+      if (nk > T(0)) P.W[idx] = P.W[idx] / nk;
+    }
+    return;
+  }
   const int pi = find_problem(prefix, count, b);
   const Prob<T> P = probs[pi];
   const int64_t KN = (int64_t)P.K * P.N;
   const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
-  if (idx >= KN) return;
-  T num = T(0), den = T(0);
-  const int slices = tc ? P.tcR : P.R;
-  for (int r = 0; r < slices; ++r) {
-    num += P.colPart[(int64_t)r * 2 * KN + idx];
-    den += P.colPart[(int64_t)r * 2 * KN + KN + idx];
-  }
-  if (mode == EPI_GRAD) { gout[idx] = den - num; return; }
-  const T base = basesel == SEL_TILDE ? P.Ht[idx] : P.H[idx];
-  const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
-  if (!isfinite(x)) atomicExch(status, 4);
-  P.H[idx] = x;
-  if (want_chi) {
-    T c1, c2;
-    chi_terms<BK, T>(x, P.Ht[idx], (T)bp.beta, c1, c2);
-    P.chiH1[idx] = c1;
-    P.chiH2[idx] = c2;
-    if (tc && P.sCH1) {
-      const int64_t k = idx / P.N, n = idx - k * P.N;
-      P.sCH1[k * P.Np + n] = tf32_round(c1);
-      P.sCH2[k * P.Np + n] = tf32_round(c2);
+  if (idx < KN && !skip) {
+    T num, den;
+    sum_slices(P.colPart + idx, 2 * KN, KN, tc ? P.tcR : P.R, num, den);
+    if (mode == EPI_GRAD) {
+      gout[idx] = den - num;
+    } else {
+      const T base = basesel == SEL_TILDE ? P.Ht[idx] : P.H[idx];
+      const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+      if (!isfinite(x)) atomicExch(status, 4);
+      if (want_chi) {
+        T c1, c2;
+        chi_terms<BK, T>(x, P.Ht[idx], (T)bp.beta, c1, c2);
+        P.chiH1[idx] = c1;
+        P.chiH2[idx] = c2;
+        if (tc && P.sCH1) {
+          const int64_t k = idx / P.N, n = idx - k * P.N;
+          P.sCH1[k * P.Np + n] = tf32_round(c1);
+          P.sCH2[k * P.Np + n] = tf32_round(c2);
+        }
+      }
+      T y = x;
+      if (fz.flags & FUSE_NORM_APPLY) {
+        const T nk = P.norms[idx / P.N];
+        if (nk > T(0)) y = x * nk;
+      }
+      P.H[idx] = y;
     }
   }
+  if (fz.flags & FUSE_LOSS) last_block_finalize<T>(fz, P, totH, nullptr);
 }
 
 // Blocks [0, totW) copy W -> Wt, blocks [totW, totW + totH) copy H -> Ht.
@@ -536,28 +682,44 @@ cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, in
 
 template <typename T, int BK>
 cudaError_t rows_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
-  rows_epilogue_kernel<T, BK><<<pl.totW, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, mode,
-                                                      basesel, want_chi, bp, gout, status, tc);
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc, const EpiFuse& fz) {
+  const int G = rows_epilogue_lanes(pl, tc);
+  if (pl.count == 1)
+    rows_epilogue_kernel<T, BK, 1024><<<rows_epilogue_grid(pl.totW, G), 1024, 0, st>>>(
+        pl.d_probs, pl.count, pl.d_prefW, mode, basesel, want_chi, bp, gout, status, tc, fz, G);
+  else
+    rows_epilogue_kernel<T, BK, EW><<<pl.totW, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, mode,
+                                                            basesel, want_chi, bp, gout, status, tc, fz, 1);
   return cudaGetLastError();
 }
 template <typename T, int BK>
 cudaError_t cols_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
-  cols_epilogue_kernel<T, BK><<<pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefH, mode,
-                                                      basesel, want_chi, bp, gout, status, tc);
+                        const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc, const EpiFuse& fz) {
+  const int grid = pl.totH + ((fz.flags & FUSE_NORM_APPLY) ? pl.totW : 0);
+  cols_epilogue_kernel<T, BK><<<grid, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefH, mode,
+                                                   basesel, want_chi, bp, gout, status, tc, fz, pl.totH);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
-  NMF_BK_DISPATCH(rows_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc)
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc,
+                                 const EpiFuse& fz) {
+  NMF_BK_DISPATCH(rows_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc, fz)
 }
 template <typename T>
 cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
-                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc) {
-  NMF_BK_DISPATCH(cols_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc)
+                                 const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc,
+                                 const EpiFuse& fz) {
+  NMF_BK_DISPATCH(cols_epi_bk, pl, mode, basesel, want_chi, bp, gout, status, st, tc, fz)
+}
+
+// W /= norms, H *= norms from P.norms (the norms a fused W epilogue produced).
+template <typename T>
+cudaError_t launch_normalize_apply(const Plan<T>& pl, const int* status, cudaStream_t st) {
+  normalize_apply_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
+                                                               pl.totW, pl.d_prefH, status);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -590,9 +752,10 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
   template cudaError_t launch_col_sweep<T>(const Plan<T>&, int, int, int, int, const BetaParams&,  \
                                            double*, const int*, cudaStream_t);                     \
   template cudaError_t launch_rows_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
-                                               T*, int*, cudaStream_t, int);                       \
+                                               T*, int*, cudaStream_t, int, const EpiFuse&);       \
   template cudaError_t launch_cols_epilogue<T>(const Plan<T>&, int, int, int, const BetaParams&,   \
-                                               T*, int*, cudaStream_t, int);                       \
+                                               T*, int*, cudaStream_t, int, const EpiFuse&);       \
+  template cudaError_t launch_normalize_apply<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \

@@ -95,7 +95,7 @@ tc_row_sweep_kernel(Prob<float> P, int wsel, int hsel, int dsel, int flags, Beta
   unsigned char* Bs = As + TILE_BYTES;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ft = blockIdx.x % P.tcRowTiles, s = blockIdx.x / P.tcRowTiles;
+  const int ft = blockIdx.x / P.tcSplitS, s = blockIdx.x % P.tcSplitS;
   const int64_t f0 = (int64_t)ft * MT;
   const int64_t nBeg = (int64_t)s * P.tcChunkN;
   const int64_t nEnd = nBeg + P.tcChunkN < P.N ? nBeg + P.tcChunkN : P.N;
@@ -263,7 +263,7 @@ tc_col_sweep_kernel(Prob<float> P, int wsel, int hsel, int csel, int flags, Beta
   unsigned char* Bs = As + TILE_BYTES;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nt = blockIdx.x % P.tcColTiles, r = blockIdx.x / P.tcColTiles;
+  const int nt = blockIdx.x / P.tcSplitR, r = blockIdx.x % P.tcSplitR;
   const int64_t n0 = (int64_t)nt * MT;
   const int64_t fBeg = (int64_t)r * P.tcChunkF;
   const int64_t fEnd = fBeg + P.tcChunkF < P.F ? fBeg + P.tcChunkF : P.F;
@@ -437,8 +437,9 @@ cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int ws
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
   if (kp <= 64 && maps && maps->ok) return launch_tc_ws_row(P, *maps, dsel, flags, bp, lossPart, status, st);
+  if (P.tcClusterS != 1) return cudaErrorNotSupported;   // clustered tilings need the warp-specialised kernel
   const size_t sm = row_smem(kp);
-  const unsigned grid = (unsigned)(P.tcRowTiles * P.tcS);
+  const unsigned grid = (unsigned)(P.tcRowTiles * P.tcSplitS);
   NMF_TC_BK_DISPATCH(tc_row_sweep_kernel, grid, sm, P, wsel, hsel, dsel, flags, bp, lossPart, status);
 }
 
@@ -448,8 +449,9 @@ cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int ws
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
   if (kp <= 64 && maps && maps->ok) return launch_tc_ws_col(P, *maps, csel, flags, bp, lossPart, status, st);
+  if (P.tcClusterR != 1) return cudaErrorNotSupported;
   const size_t sm = col_smem(kp);
-  const unsigned grid = (unsigned)(P.tcColTiles * P.tcR);
+  const unsigned grid = (unsigned)(P.tcColTiles * P.tcSplitR);
   NMF_TC_BK_DISPATCH(tc_col_sweep_kernel, grid, sm, P, wsel, hsel, csel, flags, bp, lossPart, status);
 }
 

@@ -21,6 +21,14 @@
 //                one TMEM lane and 8 of the tile's 32 streamed indices.
 // mbarriers connect the roles; every wait is bounded (1 s) and a timeout sets
 // NMF_ETIMEOUT, makes every role leave its loop, and frees the TMEM.
+//
+// Blocks that stream consecutive chunks of the same 128-wide tile form a
+// thread-block cluster of c = 1, 2, 4 or 8 blocks. Once its MMAs are done each
+// block holds a partial [P | Q] (or [Hn | Hd]) tile; the cluster adds them in a
+// fixed binary tree through distributed shared memory (rank r + s sends to rank
+// r in round s = 1, 2, 4, ...) and rank 0 writes one partial slice, so the
+// epilogue sums blocks / c slices. Blocks of a cluster never leave early:
+// every one of them reaches every cluster barrier.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -104,7 +112,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
              const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
              const __grid_constant__ CUtensorMap tmD2, int useTma, int nstages, Prob<float> P, int flags,
              BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
-  if (*status) return;
+  const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
   extern __shared__ unsigned char smem_raw[];
   __shared__ Bars bars;
   __shared__ uint32_t tslot;
@@ -116,15 +124,18 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   const int NS = nstages;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // block coordinates: the fixed 128-wide dimension (m0) and the streamed chunk [s0, s1)
-  const int tilesFixed = ROW ? P.tcRowTiles : P.tcColTiles;
-  const int mt = blockIdx.x % tilesFixed, sl = blockIdx.x / tilesFixed;
+  // (blocks of one tile are consecutive, so a cluster shares m0)
+  const int split = ROW ? P.tcSplitS : P.tcSplitR;
+  const int csize = ROW ? P.tcClusterS : P.tcClusterR;
+  const int mt = blockIdx.x / split, sl = blockIdx.x % split;
   const int64_t m0 = (int64_t)mt * MT;
   const int64_t mLim = ROW ? P.F : P.N;
   const int64_t chunk = ROW ? P.tcChunkN : P.tcChunkF;
   const int64_t sLim = ROW ? P.N : P.F;
   const int64_t s0 = (int64_t)sl * chunk;
   const int64_t s1 = s0 + chunk < sLim ? s0 + chunk : sLim;
-  const int ntiles = (int)((s1 - s0 + TL - 1) / TL);
+  // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
+  const int ntiles = (!skip && s0 < sLim) ? (int)((s1 - s0 + TL - 1) / TL) : 0;
   const bool wantLoss = flags & SWEEP_LOSS;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
   const uint32_t ncols = 256;
@@ -158,7 +169,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   if (warp < 2) {
     // ---------------- producer ----------------
     const bool leader = warp == 0 && lane == 0;
-    if (leader) {
+    if (leader && ntiles > 0) {
       mbar_arrive_expect_tx(&bars.once, (uint32_t)na * TB);
       for (int a = 0; a < na; ++a) tma_load_2d(base + L.once + a * TB, &tmOnce, 32 * a, (int)m0, &bars.once);
     }
@@ -204,7 +215,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t id_v = idesc(MT, TL, kFmtTF32), id_acc = idesc(MT, kp, kFmtTF32);
-      bool ok = role_wait(&bars.once, 0u, &s_abort, status);
+      bool ok = ntiles > 0 && role_wait(&bars.once, 0u, &s_abort, status);
       for (int t = 0; ok && t <= ntiles; ++t) {
         if (t < ntiles) {
           const int st = t % NS, b = t & 1;
@@ -304,33 +315,95 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
       fence_smem_to_async();
       mbar_arrive(&bars.abready[b]);
     }
-    if (!s_abort && ntiles > 0 && role_wait(&bars.done, 0u, &s_abort, status)) {
+  }
+
+  // ---------------- accumulators: cluster tree, then one partial slice ----------------
+  // Epilogue thread (mrow, grp) owns kp / 2 consecutive columns of [P | Q] in
+  // TMEM lane mrow: groups 0-1 the first accumulator, 2-3 the second.
+  const bool epi = warp >= EPI_WARP0;
+  const int q4 = warp & 3, grp = (warp - EPI_WARP0) >> 2;
+  const int mrow = 32 * q4 + lane;
+  const int per = kp / 2;                             // 8, 16, 24 or 32
+  const bool isQ = grp >= 2;
+  const int col0 = (grp & 1) * per;                   // first column inside P or Q
+  float acc[32];
+  #pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  if (epi) {
+    bool have = !s_abort && ntiles > 0 && role_wait(&bars.done, 0u, &s_abort, status);
+    have = __all_sync(0xffffffffu, have);             // tcgen05.ld is warp-wide
+    if (have) {
       fence_after_sync();
-      // the 2 kp accumulator columns [P | Q] split over the 4 groups
-      const int per = kp / 2;                         // multiple of 8
-      const int cbeg = grp * per;
-      const uint32_t t_cat = tbase + 128;             // P at 128, Q at 192: contiguous when kp == 64
-      for (int cc = cbeg; cc < cbeg + per; cc += 8) {
-        const bool isQ = cc >= kp;
-        const int col = isQ ? cc - kp : cc;
-        float r[8];
-        tmem_ld8((isQ ? t_acc2 : t_acc1) + lane_off + col, r);
-        tmem_ld_wait();
-        if (!mvalid) continue;
-        if (ROW) {
-          float* part = P.rowPart + (int64_t)sl * 2 * P.F * K + (isQ ? P.F * K : 0) + gm * K;
-          #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (col + j < K) part[col + j] = r[j];
-        } else {
-          const int64_t KN = (int64_t)K * P.N;
-          float* part = P.colPart + (int64_t)sl * 2 * KN + (isQ ? KN : 0) + gm;
-          #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (col + j < K) part[(int64_t)(col + j) * P.N] = r[j];
-        }
+      const uint32_t ta = (isQ ? t_acc2 : t_acc1) + ((uint32_t)(32 * q4) << 16) + col0;
+      #pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (8 * i < per) tmem_ld8(ta + 8 * i, &acc[8 * i]);
+      tmem_ld_wait();
+    }
+  }
+  if (csize > 1) {
+    const uint32_t rank = cluster_rank();
+    // Two exchange buffers of kp KB, alternating by round: the A/B tiles and
+    // the stage ring, both idle once the block's MMAs have completed (the
+    // first barrier below). Layout [float4 q][lane m] keeps the stores
+    // conflict-free.
+    cluster_sync();
+    int round = 0;
+    for (int stp = 1; stp < csize; stp <<= 1, ++round) {
+      unsigned char* buf = base + ((round & 1) ? L.stage0 : L.ab);
+      const uint32_t qbase = (uint32_t)((isQ ? per * 2 : 0) + col0) / 4;   // this thread's first float4
+      if (epi && (rank & (2 * stp - 1)) == (uint32_t)stp) {
+        const uint32_t remote = dsmem_map(buf, rank - stp);
+        #pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (4 * i < per)
+            dsmem_st4(remote + ((qbase + i) * MT + mrow) * 16u, acc[4 * i], acc[4 * i + 1], acc[4 * i + 2],
+                      acc[4 * i + 3]);
       }
-      (void)t_cat;
+      cluster_sync();
+      if (epi && (rank & (2 * stp - 1)) == 0u) {
+        #pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (4 * i < per) {
+            const float4 v = *reinterpret_cast<const float4*>(buf + ((qbase + i) * MT + mrow) * 16u);
+            acc[4 * i] += v.x; acc[4 * i + 1] += v.y; acc[4 * i + 2] += v.z; acc[4 * i + 3] += v.w;
+          }
+      }
+    }
+  }
+  if (ROW) {
+    // P and Q of rows [m0, m0 + 128) are two contiguous runs of rowPart
+    // (row-major F x K): stage them in shared memory (odd row stride, no bank
+    // conflicts) and let the whole block write them out coalesced.
+    const int Ks = K | 1;
+    float* stg = reinterpret_cast<float*>(base + L.stage0);   // idle: MMAs done, exchange rounds over
+    __syncthreads();
+    if (epi && sl % csize == 0) {
+      float* row = stg + (isQ ? MT * Ks : 0) + mrow * Ks + col0;
+      #pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < per && col0 + j < K) row[j] = acc[j];
+    }
+    __syncthreads();
+    if (sl % csize == 0) {
+      const int nrows = (int)(mLim - m0 < MT ? mLim - m0 : MT);
+      const int cnt = nrows * K;
+      float* outP = P.rowPart + (int64_t)(sl / csize) * 2 * P.F * K + m0 * K;
+      float* outQ = outP + P.F * K;
+      for (int i = tid; i < cnt; i += WS_THREADS) {
+        const int r = i / K, c = i - r * K;
+        outP[i] = stg[r * Ks + c];
+        outQ[i] = stg[MT * Ks + r * Ks + c];
+      }
+    }
+  } else if (epi && sl % csize == 0) {
+    const int64_t gm = m0 + mrow;
+    if (gm < mLim) {
+      const int64_t KN = (int64_t)K * P.N;
+      float* part = P.colPart + (int64_t)(sl / csize) * 2 * KN + (isQ ? KN : 0) + (int64_t)col0 * P.N + gm;
+      #pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < per && col0 + j < K) part[(int64_t)j * P.N] = acc[j];
     }
   }
   if (wantLoss) {
@@ -398,26 +471,41 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   const CUtensorMap& fa = ROW ? m.htB : m.wsB;
   const CUtensorMap& d1 = ROW ? (CHI ? m.ch1 : m.hs) : (CHI ? m.cw1 : m.wt);
   const CUtensorMap& d2 = ROW ? (CHI ? m.ch2 : m.hs) : (CHI ? m.cw2 : m.wt);
-  const size_t sm = 1024 + ws_layout(kp, CHI, ns).total;
-  const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcS : P.tcColTiles * P.tcR);
+  const WsLayout lay = ws_layout(kp, CHI, ns);
+  const size_t sm = 1024 + lay.total;
+  const int csize = ROW ? P.tcClusterS : P.tcClusterR;
+  // the cluster exchange buffers (A/B tiles, stage ring) each hold kp KB
+  if (csize > 1 && ((uint32_t)ns * lay.stage_bytes < 1024u * kp || 4 * TB < 1024u * kp)) return cudaErrorInvalidValue;
+  // the row sweep stages its [P | Q] tile (2 x 128 x (K | 1) floats) over the stage ring and the A/B tiles
+  if (ROW && lay.total - lay.stage0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcSplitS : P.tcColTiles * P.tcSplitR);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(WS_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaError_t e = cudaSuccess;
-#define NMF_WS_CASE(BKV)                                                                                  \
-  case BKV:                                                                                               \
-    e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                             \
-    if (e == cudaSuccess)                                                                                 \
-      tc_ws_kernel<BKV, CHI, ROW><<<grid, WS_THREADS, sm, st>>>(tmV, once, fa, d1, d2, useTma, ns, P, flags, bp, \
-                                                                 lossPart, status);                        \
+#define NMF_WS_CASE(BKV)                                                                                   \
+  case BKV:                                                                                                \
+    e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                              \
+    if (e == cudaSuccess)                                                                                  \
+      e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, ns, P, flags, bp, \
+                             lossPart, status);                                                            \
     break;
   switch (bp.kind) {
     NMF_WS_CASE(BK_IS)
     NMF_WS_CASE(BK_KL)
     NMF_WS_CASE(BK_EUC)
     NMF_WS_CASE(BK_B15)
-    default:
-      e = prep(tc_ws_kernel<BK_GENERAL, CHI, ROW>, sm);
-      if (e == cudaSuccess)
-        tc_ws_kernel<BK_GENERAL, CHI, ROW><<<grid, WS_THREADS, sm, st>>>(tmV, once, fa, d1, d2, useTma, ns, P, flags,
-                                                                          bp, lossPart, status);
+    NMF_WS_CASE(BK_GENERAL)
   }
 #undef NMF_WS_CASE
   if (e != cudaSuccess) return e;
@@ -445,6 +533,36 @@ bool tc_build_maps(const Prob<float>& P, TcMaps* m) {
   ok = ok && map2d(&m->cw2, P.sCW2, F, kp, P.Fp, 32, kp, SW);
   m->ok = ok;
   return ok;
+}
+
+int tc_ws_capacity(int kp, int csize) {
+  if (kp > 64 || kp < 16) return 0;
+  const int ns = pick_stages(kp, true);
+  if (ns == 0) return 0;
+  const size_t sm = 1024 + ws_layout(kp, true, ns).total;
+  auto kern = tc_ws_kernel<BK_GENERAL, true, true>;
+  if (prep(kern, sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(csize * 64));
+  cfg.blockDim = dim3(WS_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n * csize;
 }
 
 cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, int flags, const BetaParams& bp,

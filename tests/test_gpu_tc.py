@@ -117,3 +117,20 @@ def test_tf32_spectrogram_full_size(lib):
     assert maxrel(W, Wo) < TF32_RTOL
     assert maxrel(H, Ho) < TF32_RTOL
     assert loss == pytest.approx(lo[0], rel=TF32_LOSS_RTOL)
+
+
+@pytest.mark.parametrize("cluster,K,method,order", [(2, 40, "jmm", "W"), (4, 64, "jmm", "H"), (8, 20, "jmm", "W"),
+                                                    (8, 33, "bmm", "H")])
+def test_tf32_cluster_reduction(lib, monkeypatch, cluster, K, method, order):
+    """Blocks of a tile in clusters of 2/4/8 combined through distributed
+    shared memory (padding blocks included) give the oracle's iterate."""
+    monkeypatch.setenv("NMF_TC_CLUSTER", str(cluster))
+    V, W0, H0 = problem(300, 2100, K, seed=3)
+    W, H, loss, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
+    Wo, Ho, lo = O.run(V, W0, H0, 1.0, method=method, iters=2, order=order)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[1], rel=TF32_LOSS_RTOL)
+    monkeypatch.delenv("NMF_TC_CLUSTER")
+    W1, H1, _, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
+    assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
