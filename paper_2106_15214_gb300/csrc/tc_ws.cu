@@ -7,18 +7,25 @@
 // with every product on the tensor cores (tcgen05 kind::tf32, FP32 in TMEM).
 //
 // Roles (20 warps):
-//   warp 0 (+1)  producer: TMA loads of each tile's operands into a ring of
-//                stages (V by TMA when its rows are 16-byte aligned, else by
-//                cp.async from warps 0-1); the factor operands come from the
-//                TF32 shadow copies, already in the 128B-swizzled K-major
-//                layout the MMAs read.
-//   warp 2       MMA issuer (one thread): MMA1 of tile t into a double-buffered
-//                TMEM tile, then MMA2/MMA3 of tile t-1 from the A/B tiles the
-//                epilogue produced, so the tensor core never waits on the
-//                CUDA cores and vice versa.
-//   warps 4-19   epilogue: TMEM -> registers, the powers (and the objective),
-//                A and B into a double-buffered shared tile; each thread owns
-//                one TMEM lane and 8 of the tile's 32 streamed indices.
+//   warp 0       operand producer: TMA loads of the MMA1 A tile (once per
+//                block) and, per tile, of the B operands of MMA1/2/3 into a
+//                ring of operand slots; they come from the TF32 shadow copies,
+//                already in the 128B-swizzled K-major layout the MMAs read.
+//   warp 1       V producer: the V tile of each tile step into its own ring
+//                (TMA when V's rows are 16-byte aligned, else cp.async).
+//   warp 2       MMA issuer (converged warp, an elected lane issues): MMA1
+//                of tile t into one of 4 TMEM Vt buffers as soon as its
+//                operands are in, MMA2/MMA3 of a tile as soon as its A/B
+//                tiles are, so the tensor core and the CUDA cores overlap.
+//                Every A operand is read from TMEM (the MMA1 tile, moved
+//                there once, and the epilogue's A/B tiles): about 2.5x the
+//                issue rate of shared-memory A operands, and no shared-memory
+//                traffic for them.
+//   warps 4-19   epilogue: Vt from TMEM and V from shared memory to
+//                registers, the powers (and the objective), A and B back to
+//                TMEM. Two groups of 8 warps take alternate tiles; each
+//                thread owns one TMEM lane and 16 of the tile's 32 streamed
+//                indices.
 // mbarriers connect the roles; every wait is bounded (1 s) and a timeout sets
 // NMF_ETIMEOUT, makes every role leave its loop, and frees the TMEM.
 //
@@ -49,39 +56,53 @@ constexpr int MT = 128;
 constexpr uint32_t TB = 16384;
 constexpr int EPI_WARP0 = 4;
 constexpr uint32_t EPI_THREADS = 512;
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_OP = 8;          // operand ring slots
+constexpr int MAX_V = 6;           // V ring slots
+constexpr int NVT = 4;             // TMEM buffers for Vt tiles
 constexpr int ETIMEOUT = 5;
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+// TMEM columns (512 allocated): Vt tiles 32 b (b < 4), the A/B tiles of
+// epilogue group g at 128 + 64 g and 160 + 64 g, the accumulators at 256 and
+// 320, the A operand of MMA1 at 384 (kp <= 64 columns).
+constexpr uint32_t TM_AB = 128, TM_ACC1 = 256, TM_ACC2 = 320, TM_ONCE = 384, TM_COLS = 512;
 
+// Shared memory: the A operand of MMA1 as loaded (it moves on to TMEM), a
+// ring of MMA operand slots (B of MMA1, B of MMA2, B of MMA3 for one tile)
+// and a ring of V tiles. V has its own ring because the epilogue is done with
+// it long before MMA2/3 are done with the operands.
 struct WsLayout {
-  uint32_t once;                 // A operand of MMA1, loaded once per block
-  uint32_t stage0, stage_bytes;  // stage s at stage0 + s * stage_bytes: V, B of MMA1, B of MMA2, B of MMA3
+  uint32_t once;
+  uint32_t op0, op_bytes;        // operand slot s at op0 + s * op_bytes
   uint32_t off_fa, off_d1, off_d2;
-  uint32_t ab;                   // A0, B0, A1, B1 tiles (16 KB each)
+  uint32_t v0;                   // V slot s at v0 + s * TB
   uint32_t total;
-  int nstages;
 };
 
-__host__ __device__ inline WsLayout ws_layout(int kp, bool chi, int nstages) {
+__host__ __device__ inline WsLayout ws_layout(int kp, bool chi, int nop, int nv) {
   WsLayout L;
   const uint32_t na = (kp + 31) / 32;
   L.once = 0;
-  L.stage0 = na * TB;
-  L.off_fa = TB;
-  L.off_d1 = TB + na * (TL * 128u);
+  L.op0 = na * TB;
+  L.off_fa = 0;
+  L.off_d1 = na * (TL * 128u);
   L.off_d2 = chi ? L.off_d1 + (uint32_t)kp * 128u : L.off_d1;
-  L.stage_bytes = L.off_d1 + (uint32_t)kp * 128u * (chi ? 2u : 1u);
-  L.stage_bytes = (L.stage_bytes + 1023u) & ~1023u;
-  L.ab = L.stage0 + nstages * L.stage_bytes;
-  L.total = L.ab + 4 * TB;
-  L.nstages = nstages;
+  L.op_bytes = L.off_d1 + (uint32_t)kp * 128u * (chi ? 2u : 1u);
+  L.op_bytes = (L.op_bytes + 1023u) & ~1023u;
+  L.v0 = L.op0 + nop * L.op_bytes;
+  L.total = L.v0 + nv * TB;
   return L;
 }
 
-inline int pick_stages(int kp, bool chi) {
-  for (int s = MAX_STAGES; s >= 2; --s)
-    if (1024 + ws_layout(kp, chi, s).total + 1024 <= SMEM_LIMIT) return s;
-  return 0;
+// Deepest rings that fit: as many V slots as leave room for >= 4 operand slots.
+inline bool pick_rings(int kp, bool chi, int* nop, int* nv) {
+  for (int v = MAX_V; v >= 2; --v)
+    for (int o = MAX_OP; o >= (v <= 3 ? 2 : 4); --o)
+      if (1024 + ws_layout(kp, chi, o, v).total + 1024 <= SMEM_LIMIT) {
+        *nop = o;
+        *nv = v;
+        return true;
+      }
+  return false;
 }
 
 // Bounded wait shared by every role: gives up on timeout or when another role
@@ -101,7 +122,8 @@ __device__ __forceinline__ bool role_wait(uint64_t* bar, uint32_t parity, volati
 }
 
 struct Bars {
-  uint64_t full[MAX_STAGES], empty[MAX_STAGES], vfull[2], vfree[2], abready[2], abfree[2], once, done;
+  uint64_t opfull[MAX_OP], opempty[MAX_OP], vfull[MAX_V], vempty[MAX_V];
+  uint64_t tfull[NVT], tfree[NVT], abready[2], abfree[2], once, onceT, done;
 };
 
 // ROW = true: row sweep (M = 128 rows f, tiles of 32 columns n).
@@ -110,7 +132,7 @@ template <int BK, bool CHI, bool ROW>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmOnce,
              const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
-             const __grid_constant__ CUtensorMap tmD2, int useTma, int nstages, Prob<float> P, int flags,
+             const __grid_constant__ CUtensorMap tmD2, int useTma, int nop, int nv, Prob<float> P, int flags,
              BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
   const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
   extern __shared__ unsigned char smem_raw[];
@@ -120,8 +142,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   __shared__ double red[32];
   const int K = P.K, kp = (K + 15) & ~15, na = (kp + 31) / 32;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const WsLayout L = ws_layout(kp, CHI, nstages);
-  const int NS = nstages;
+  const WsLayout L = ws_layout(kp, CHI, nop, nv);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // block coordinates: the fixed 128-wide dimension (m0) and the streamed chunk [s0, s1)
   // (blocks of one tile are consecutive, so a cluster shares m0)
@@ -138,23 +159,30 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   const int ntiles = (!skip && s0 < sLim) ? (int)((s1 - s0 + TL - 1) / TL) : 0;
   const bool wantLoss = flags & SWEEP_LOSS;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
-  const uint32_t ncols = 256;
+  const uint32_t ncols = TM_COLS;
   const uint32_t faBytes = (uint32_t)na * TL * 128u, dBytes = (uint32_t)kp * 128u;
-  const uint32_t stageTx = (useTma ? TB : 0u) + faBytes + dBytes * (CHI ? 2u : 1u);
+  const uint32_t opTx = faBytes + dBytes * (CHI ? 2u : 1u);
 
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(&bars.full[s], useTma ? 1u : 65u);
-      mbar_init(&bars.empty[s], 1u);
+    for (int s = 0; s < nop; ++s) {
+      mbar_init(&bars.opfull[s], 1u);
+      mbar_init(&bars.opempty[s], 1u);
+    }
+    for (int s = 0; s < nv; ++s) {
+      mbar_init(&bars.vfull[s], useTma ? 1u : 32u);
+      mbar_init(&bars.vempty[s], EPI_THREADS / 64);   // the 8 warps of the group that reads the tile
+    }
+    for (int b = 0; b < NVT; ++b) {
+      mbar_init(&bars.tfull[b], 1u);
+      mbar_init(&bars.tfree[b], EPI_THREADS / 64);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&bars.vfull[b], 1u);
-      mbar_init(&bars.vfree[b], EPI_THREADS);
-      mbar_init(&bars.abready[b], EPI_THREADS);
+      mbar_init(&bars.abready[b], EPI_THREADS / 64);
       mbar_init(&bars.abfree[b], 1u);
     }
     mbar_init(&bars.once, 1u);
+    mbar_init(&bars.onceT, 4u);                      // epilogue warps 4-7 after moving it to TMEM
     mbar_init(&bars.done, 1u);
     fence_mbar_init();
   }
@@ -163,157 +191,274 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tslot;
-  const uint32_t t_acc1 = tbase + 128, t_acc2 = tbase + 192;   // P | Hn, Q | Hd
+  const uint32_t t_acc1 = tbase + TM_ACC1, t_acc2 = tbase + TM_ACC2;   // P | Hn, Q | Hd
   double loss = 0.0;
 
-  if (warp < 2) {
-    // ---------------- producer ----------------
-    const bool leader = warp == 0 && lane == 0;
-    if (leader && ntiles > 0) {
-      mbar_arrive_expect_tx(&bars.once, (uint32_t)na * TB);
-      for (int a = 0; a < na; ++a) tma_load_2d(base + L.once + a * TB, &tmOnce, 32 * a, (int)m0, &bars.once);
-    }
-    for (int t = 0; t < ntiles; ++t) {
-      const int st = t % NS;
-      const int64_t c0 = s0 + (int64_t)t * TL;     // first streamed index of the tile
-      if (t >= NS && !role_wait(&bars.empty[st], (uint32_t)(t / NS - 1) & 1u, &s_abort, status)) break;
-      unsigned char* sb = base + L.stage0 + st * L.stage_bytes;
-      if (leader) {
-        mbar_arrive_expect_tx(&bars.full[st], stageTx);
-        if (useTma) {
-          if (ROW) tma_load_2d(sb, &tmV, (int)c0, (int)m0, &bars.full[st]);
-          else tma_load_2d(sb, &tmV, (int)m0, (int)c0, &bars.full[st]);
-        }
-        for (int a = 0; a < na; ++a) tma_load_2d(sb + L.off_fa + a * (TL * 128), &tmFa, 32 * a, (int)c0, &bars.full[st]);
-        tma_load_2d(sb + L.off_d1, &tmD1, (int)c0, 0, &bars.full[st]);
-        if (CHI) tma_load_2d(sb + L.off_d2, &tmD2, (int)c0, 0, &bars.full[st]);
+  if (warp == 0) {
+    // ---------------- operand producer: the once tile, then a slot per tile ----------------
+    // (the warp runs the loop converged; one elected lane issues each copy)
+    if (ntiles > 0) {
+      if (elect_one()) {
+        mbar_arrive_expect_tx(&bars.once, (uint32_t)na * TB);
+        for (int a = 0; a < na; ++a) tma_load_2d(base + L.once + a * TB, &tmOnce, 32 * a, (int)m0, &bars.once);
       }
-      if (!useTma) {
-        const int pl = tid;                          // 0..63
-        for (int j = 0; j < (MT * TL) / 64; ++j) {
-          const int i = pl + 64 * j;
+      int st = 0;
+      uint32_t ph = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int c0 = (int)(s0 + (int64_t)t * TL);   // first streamed index of the tile
+        if (t >= nop && !__all_sync(0xffffffffu, role_wait(&bars.opempty[st], ph ^ 1u, &s_abort, status))) break;
+        unsigned char* sb = base + L.op0 + st * L.op_bytes;
+        if (elect_one()) {
+          mbar_arrive_expect_tx(&bars.opfull[st], opTx);
+          for (int a = 0; a < na; ++a)
+            tma_load_2d(sb + L.off_fa + a * (TL * 128), &tmFa, 32 * a, c0, &bars.opfull[st]);
+          tma_load_2d(sb + L.off_d1, &tmD1, c0, 0, &bars.opfull[st]);
+          if (CHI) tma_load_2d(sb + L.off_d2, &tmD2, c0, 0, &bars.opfull[st]);
+        }
+        __syncwarp();
+        if (++st == nop) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- V producer: TMA from an elected lane, else cp.async from the warp ----------------
+    int st = 0;
+    uint32_t ph = 0;
+    for (int t = 0; t < ntiles; ++t) {
+      const int64_t c0 = s0 + (int64_t)t * TL;
+      if (t >= nv && !__all_sync(0xffffffffu, role_wait(&bars.vempty[st], ph ^ 1u, &s_abort, status))) break;
+      unsigned char* vb = base + L.v0 + st * TB;
+      if (useTma) {
+        if (elect_one()) {
+          mbar_arrive_expect_tx(&bars.vfull[st], TB);
+          if (ROW) tma_load_2d(vb, &tmV, (int)c0, (int)m0, &bars.vfull[st]);
+          else tma_load_2d(vb, &tmV, (int)m0, (int)c0, &bars.vfull[st]);
+        }
+        __syncwarp();
+      } else {
+        for (int j = 0; j < (MT * TL) / 32; ++j) {
+          const int i = lane + 32 * j;
           int64_t gf, gn;
           uint32_t off;
-          bool ok;
+          bool in;
           if (ROW) {
             const int f = i >> 5, n = i & 31;
             gf = m0 + f; gn = c0 + n;
-            ok = gf < P.F && gn < s1;
+            in = gf < P.F && gn < s1;
             off = sw128_offset(f, 4 * n);
           } else {
             const int f = i >> 7, n = i & 127;
             gf = c0 + f; gn = m0 + n;
-            ok = gf < s1 && gn < P.N;
+            in = gf < s1 && gn < P.N;
             off = 4u * i;
           }
-          cp_async4(sb + off, ok ? (const void*)(P.V + gf * P.ldv + gn) : (const void*)P.V, ok ? 4u : 0u);
+          cp_async4(vb + off, in ? (const void*)(P.V + gf * P.ldv + gn) : (const void*)P.V, in ? 4u : 0u);
         }
-        cp_async_mbar_arrive(&bars.full[st]);
+        cp_async_mbar_arrive(&bars.vfull[st]);
+      }
+      if (++st == nv) {
+        st = 0;
+        ph ^= 1u;
       }
     }
   } else if (warp == 2) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      const uint32_t id_v = idesc(MT, TL, kFmtTF32), id_acc = idesc(MT, kp, kFmtTF32);
-      bool ok = ntiles > 0 && role_wait(&bars.once, 0u, &s_abort, status);
-      for (int t = 0; ok && t <= ntiles; ++t) {
-        if (t < ntiles) {
-          const int st = t % NS, b = t & 1;
-          if (!role_wait(&bars.full[st], (uint32_t)(t / NS) & 1u, &s_abort, status)) break;
-          if (t >= 2 && !role_wait(&bars.vfree[b], (uint32_t)((t - 2) >> 1) & 1u, &s_abort, status)) break;
-          fence_after_sync();
-          const unsigned char* sb = base + L.stage0 + st * L.stage_bytes;
-          for (int ks = 0; ks < kp / 8; ++ks) {
-            const int k0 = ks * 8;
-            const uint32_t within = (uint32_t)(k0 & 31) * 4u;
-            mma_tf32(tbase + 32 * b, desc_sw128(smem_u32(base + L.once + (k0 >> 5) * TB) + within),
-                     desc_sw128(smem_u32(sb + L.off_fa + (k0 >> 5) * (TL * 128)) + within), id_v, ks > 0);
+    // The warp polls both queues converged (an elected lane issues each
+    // tcgen05 instruction): MMA1 of tile t1 (Vt into TMEM buffer t1 % 4) as
+    // soon as its operand slot is loaded and the buffer is free, MMA2/3 of
+    // tile t2 as soon as the epilogue has written its A/B tiles. The A
+    // operands of all three come from TMEM, the B operands from shared
+    // memory. Descriptors are built once; an operand at byte offset o is the
+    // base descriptor plus o / 16 (the start-address field, bits 0-13, cannot
+    // carry below 256 KB).
+    const uint32_t id_v = idesc(MT, TL, kFmtTF32), id_acc = idesc(MT, kp, kFmtTF32);
+    const uint64_t dOp = desc_sw128(smem_u32(base + L.op0));
+    const uint32_t op16 = L.op_bytes >> 4;
+    int t1 = 0, t2 = 0, so1 = 0, so2 = 0;
+    uint32_t ph1 = 0;
+    uint64_t idle0 = 0;
+    bool ok = ntiles > 0 && role_wait(&bars.onceT, 0u, &s_abort, status);
+    ok = __all_sync(0xffffffffu, ok);
+    fence_after_sync();
+    while (ok && t2 < ntiles) {
+      bool prog = false;
+      bool can1 = t1 < ntiles && mbar_test(&bars.opfull[so1], ph1) &&
+                  (t1 < NVT || mbar_test(&bars.tfree[t1 & 3], (uint32_t)((t1 - NVT) >> 2) & 1u));
+      can1 = __shfl_sync(0xffffffffu, can1, 0);
+      if (can1) {
+        fence_after_sync();
+        const uint64_t dFa = dOp + (uint64_t)(so1 * op16 + (L.off_fa >> 4));
+        const uint32_t dv = tbase + 32 * (t1 & 3);
+        // unrolled (offsets fold to constants): the MMA warp shares its
+        // scheduler with four busy epilogue warps, so every instruction counts
+        #pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          if (ks < kp / 8) {
+            const uint32_t k0 = (uint32_t)ks * 8u;
+            const uint64_t db = dFa + (((k0 >> 5) * (uint32_t)(TL * 128) + (k0 & 31u) * 4u) >> 4);
+            if (elect_one()) mma_tf32_ts(dv, tbase + TM_ONCE + k0, db, id_v, ks > 0);
           }
-          mma_commit(&bars.vfull[b]);
         }
-        if (t >= 1) {
-          const int u = t - 1, bu = u & 1, su = u % NS;
-          if (!role_wait(&bars.abready[bu], (uint32_t)(u >> 1) & 1u, &s_abort, status)) break;
-          fence_after_sync();
-          const unsigned char* sb = base + L.stage0 + su * L.stage_bytes;
-          const unsigned char* As = base + L.ab + bu * 2 * TB;
-          const unsigned char* Bs = As + TB;
-          for (int ks = 0; ks < TL / 8; ++ks) {
-            const uint32_t within = (uint32_t)ks * 32u;
-            const uint32_t acc = (u > 0 || ks > 0) ? 1u : 0u;
-            mma_tf32(t_acc1, desc_sw128(smem_u32(As) + within), desc_sw128(smem_u32(sb + L.off_d1) + within), id_acc, acc);
-            mma_tf32(t_acc2, desc_sw128(smem_u32(Bs) + within), desc_sw128(smem_u32(sb + L.off_d2) + within), id_acc, acc);
-          }
-          mma_commit(&bars.abfree[bu]);
-          mma_commit(&bars.empty[su]);
+        if (elect_one()) mma_commit(&bars.tfull[t1 & 3]);
+        __syncwarp();
+        ++t1;
+        if (++so1 == nop) {
+          so1 = 0;
+          ph1 ^= 1u;
         }
+        prog = true;
       }
-      mma_commit(&bars.done);
+      bool can2 = t2 < t1 && mbar_test(&bars.abready[t2 & 1], (uint32_t)(t2 >> 1) & 1u);
+      can2 = __shfl_sync(0xffffffffu, can2, 0);
+      if (can2) {
+        fence_after_sync();
+        const int b = t2 & 1;
+        const uint32_t tA = tbase + TM_AB + 64u * b, tB = tA + 32u;
+        const uint64_t dD1 = dOp + (uint64_t)(so2 * op16 + (L.off_d1 >> 4));
+        const uint64_t dD2 = dOp + (uint64_t)(so2 * op16 + (L.off_d2 >> 4));
+        #pragma unroll
+        for (int ks = 0; ks < TL / 8; ++ks) {
+          const uint32_t acc = (t2 > 0 || ks > 0) ? 1u : 0u;
+          if (elect_one()) mma_tf32_ts(t_acc1, tA + 8u * ks, dD1 + 2u * ks, id_acc, acc);   // 32 bytes along K
+          if (elect_one()) mma_tf32_ts(t_acc2, tB + 8u * ks, dD2 + 2u * ks, id_acc, acc);
+        }
+        if (elect_one()) {
+          mma_commit(&bars.abfree[b]);
+          mma_commit(&bars.opempty[so2]);
+        }
+        __syncwarp();
+        ++t2;
+        if (++so2 == nop) so2 = 0;
+        prog = true;
+      }
+      if (prog) {
+        idle0 = 0;
+      } else {
+        const bool ab = s_abort != 0;
+        const uint64_t now = globaltimer_ns();
+        if (!idle0) idle0 = now;
+        bool quit = ab || now - idle0 > 1000000000ull;
+        quit = __shfl_sync(0xffffffffu, quit, 0);
+        if (quit) {
+          if (!ab && lane == 0) {
+            s_abort = 1;
+            atomicExch(status, ETIMEOUT);
+          }
+          break;
+        }
+        __nanosleep(32);
+      }
     }
+    if (elect_one()) mma_commit(&bars.done);
+    __syncwarp();
   } else if (warp >= EPI_WARP0) {
     // ---------------- epilogue ----------------
-    const int q4 = warp & 3, grp = (warp - EPI_WARP0) >> 2;   // TMEM lane quarter, group of 8 streamed indices
+    // Two groups of 8 warps take alternate tiles (group g: tiles g, g + 2, ...;
+    // A/B buffer g), so one group's waits overlap the other's work. Within a
+    // group, warp (q4, half) owns TMEM lanes 32 q4 .. 32 q4 + 31 and streamed
+    // indices 16 half .. 16 half + 15.
+    const int ew = warp - EPI_WARP0;
+    const int q4 = warp & 3;
+    const int g = (ew >> 2) & 1, half = ew >> 3;
     const int mrow = 32 * q4 + lane;                          // this thread's TMEM lane
     const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
     const int64_t gm = m0 + mrow;
     const bool mvalid = gm < mLim;
-    const int jb0 = 8 * grp;
-    for (int t = 0; t < ntiles; ++t) {
-      const int st = t % NS, b = t & 1;
+    const int jb0 = 16 * half;
+    const float beta = (float)bp.beta;
+    const uint32_t tA = tbase + TM_AB + 64u * g + lane_off + jb0, tB = tA + 32u;
+    if (ew < 4 && ntiles > 0) {
+      // warps 4-7 move the A operand of MMA1 (row mrow, kp columns) from shared memory to TMEM
+      if (__all_sync(0xffffffffu, role_wait(&bars.once, 0u, &s_abort, status))) {
+        for (int k0 = 0; k0 < kp; k0 += 16) {
+          const unsigned char* src = base + L.once + (k0 >> 5) * TB;
+          float o[16];
+          #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 v4 = *reinterpret_cast<const float4*>(src + sw128_offset(mrow, 4 * (k0 & 31) + 16 * i));
+            o[4 * i] = v4.x; o[4 * i + 1] = v4.y; o[4 * i + 2] = v4.z; o[4 * i + 3] = v4.w;
+          }
+          tmem_st16(tbase + TM_ONCE + lane_off + k0, o);
+        }
+        tmem_st_wait();
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.onceT);
+      }
+    }
+    int sv = g;                                               // nv >= 2: tile g sits in V slot g, phase 0
+    uint32_t pv = 0;
+    for (int t = g; t < ntiles; t += 2) {
+      const int tb = t & 3;
       const int64_t c0 = s0 + (int64_t)t * TL;
       const int nvalid = (int)((s1 - c0) < TL ? (s1 - c0) : TL);   // streamed indices of this tile inside the chunk
-      if (!role_wait(&bars.vfull[b], (uint32_t)(t >> 1) & 1u, &s_abort, status)) break;
-      if (!role_wait(&bars.full[st], (uint32_t)(t / NS) & 1u, &s_abort, status)) break;
+      // waits decided warp-wide (the warp arrives once and tcgen05.ld is warp-wide)
+      if (!__all_sync(0xffffffffu, role_wait(&bars.tfull[tb], (uint32_t)(t >> 2) & 1u, &s_abort, status))) break;
+      if (!__all_sync(0xffffffffu, role_wait(&bars.vfull[sv], pv, &s_abort, status))) break;
       fence_after_sync();
-      float vt[8];
-      tmem_ld8(tbase + 32 * b + lane_off + jb0, vt);
+      float vt[16];
+      tmem_ld16(tbase + 32 * tb + lane_off + jb0, vt);
+      const unsigned char* vb = base + L.v0 + sv * TB;
+      float vv[16];
+      if (ROW) {
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v4 = *reinterpret_cast<const float4*>(vb + sw128_offset(mrow, 4 * jb0 + 16 * i));
+          vv[4 * i] = v4.x; vv[4 * i + 1] = v4.y; vv[4 * i + 2] = v4.z; vv[4 * i + 3] = v4.w;
+        }
+      } else {
+        const float* Vs = reinterpret_cast<const float*>(vb) + mrow;
+        #pragma unroll
+        for (int j = 0; j < 16; ++j) vv[j] = Vs[(jb0 + j) * MT];
+      }
       tmem_ld_wait();
       fence_before_sync();
-      mbar_arrive(&bars.vfree[b]);
-      if (t >= 2 && !role_wait(&bars.abfree[b], (uint32_t)((t - 2) >> 1) & 1u, &s_abort, status)) break;
-      const unsigned char* sb = base + L.stage0 + st * L.stage_bytes;
-      unsigned char* As = base + L.ab + b * 2 * TB;
-      unsigned char* Bs = As + TB;
-      float vv[8];
-      if (ROW) {
-        const float4 v0 = *reinterpret_cast<const float4*>(sb + sw128_offset(mrow, 4 * jb0));
-        const float4 v1 = *reinterpret_cast<const float4*>(sb + sw128_offset(mrow, 4 * jb0 + 16));
-        vv[0] = v0.x; vv[1] = v0.y; vv[2] = v0.z; vv[3] = v0.w;
-        vv[4] = v1.x; vv[5] = v1.y; vv[6] = v1.z; vv[7] = v1.w;
-      } else {
-        const float* Vs = reinterpret_cast<const float*>(sb) + mrow;
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) vv[j] = Vs[(jb0 + j) * MT];
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars.tfree[tb]);
+        mbar_arrive(&bars.vempty[sv]);
       }
-      float a[8], bb[8];
+      if (t >= 2 && !__all_sync(0xffffffffu, role_wait(&bars.abfree[g], (uint32_t)((t - 2) >> 1) & 1u, &s_abort, status)))
+        break;
       float tl = 0.f;
-      if (mvalid && jb0 + 8 <= nvalid) {             // every entry of this thread's group is inside
+      if (mvalid && jb0 + 16 <= nvalid) {            // every entry of this thread is inside
         #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 16; ++j) {
           const float v = vv[j] + kappa, y = vt[j] + kappa;
-          ab_terms_fast<BK>(v, y, bm2, a[j], bb[j]);
-          if (wantLoss) tl += dbeta_fast<BK>(v, y, (float)bp.beta, bp.series);
+          if (wantLoss) tl += dbeta_fast<BK>(v, y, beta, bp.series);
+          ab_terms_fast<BK>(v, y, bm2, vv[j], vt[j]);     // A into vv, B into vt
         }
       } else {
         #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          a[j] = 0.f;
-          bb[j] = 0.f;
+        for (int j = 0; j < 16; ++j) {
+          const float v = vv[j] + kappa, y = vt[j] + kappa;
+          vv[j] = 0.f;
+          vt[j] = 0.f;
           if (mvalid && jb0 + j < nvalid) {
-            const float v = vv[j] + kappa, y = vt[j] + kappa;
-            ab_terms_fast<BK>(v, y, bm2, a[j], bb[j]);
-            if (wantLoss) tl += dbeta_fast<BK>(v, y, (float)bp.beta, bp.series);
+            if (wantLoss) tl += dbeta_fast<BK>(v, y, beta, bp.series);
+            ab_terms_fast<BK>(v, y, bm2, vv[j], vt[j]);
           }
         }
       }
-      const uint32_t off0 = sw128_offset(mrow, 4 * jb0), off1 = sw128_offset(mrow, 4 * jb0 + 16);
-      *reinterpret_cast<float4*>(As + off0) = make_float4(to_tf32(a[0]), to_tf32(a[1]), to_tf32(a[2]), to_tf32(a[3]));
-      *reinterpret_cast<float4*>(As + off1) = make_float4(to_tf32(a[4]), to_tf32(a[5]), to_tf32(a[6]), to_tf32(a[7]));
-      *reinterpret_cast<float4*>(Bs + off0) = make_float4(to_tf32(bb[0]), to_tf32(bb[1]), to_tf32(bb[2]), to_tf32(bb[3]));
-      *reinterpret_cast<float4*>(Bs + off1) = make_float4(to_tf32(bb[4]), to_tf32(bb[5]), to_tf32(bb[6]), to_tf32(bb[7]));
-      loss += (double)tl;
-      fence_smem_to_async();
-      mbar_arrive(&bars.abready[b]);
+      #pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        vv[j] = to_tf32(vv[j]);
+        vt[j] = to_tf32(vt[j]);
+      }
+      tmem_st16(tA, vv);
+      tmem_st16(tB, vt);
+      if (wantLoss) loss += (double)tl;
+      tmem_st_wait();
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.abready[g]);
+      sv += 2;
+      if (sv >= nv) {
+        sv -= nv;
+        pv ^= 1u;
+      }
     }
   }
 
@@ -343,14 +488,13 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   }
   if (csize > 1) {
     const uint32_t rank = cluster_rank();
-    // Two exchange buffers of kp KB, alternating by round: the A/B tiles and
-    // the stage ring, both idle once the block's MMAs have completed (the
-    // first barrier below). Layout [float4 q][lane m] keeps the stores
-    // conflict-free.
+    // Two exchange buffers of kp KB, alternating by round, over the rings
+    // (idle once the block's MMAs have completed: the first barrier below).
+    // Layout [float4 q][lane m] keeps the stores conflict-free.
     cluster_sync();
     int round = 0;
     for (int stp = 1; stp < csize; stp <<= 1, ++round) {
-      unsigned char* buf = base + ((round & 1) ? L.stage0 : L.ab);
+      unsigned char* buf = base + L.op0 + ((round & 1) ? 1024u * kp : 0u);
       const uint32_t qbase = (uint32_t)((isQ ? per * 2 : 0) + col0) / 4;   // this thread's first float4
       if (epi && (rank & (2 * stp - 1)) == (uint32_t)stp) {
         const uint32_t remote = dsmem_map(buf, rank - stp);
@@ -376,7 +520,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     // (row-major F x K): stage them in shared memory (odd row stride, no bank
     // conflicts) and let the whole block write them out coalesced.
     const int Ks = K | 1;
-    float* stg = reinterpret_cast<float*>(base + L.stage0);   // idle: MMAs done, exchange rounds over
+    float* stg = reinterpret_cast<float*>(base + L.op0);   // rings idle: MMAs done, exchange over
     __syncthreads();
     if (epi && sl % csize == 0) {
       float* row = stg + (isQ ? MT * Ks : 0) + mrow * Ks + col0;
@@ -461,8 +605,8 @@ template <bool CHI, bool ROW>
 cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const BetaParams& bp, double* lossPart,
                       int* status, cudaStream_t st) {
   const int kp = P.kp;
-  const int ns = pick_stages(kp, CHI);
-  if (ns == 0) return cudaErrorInvalidValue;
+  int nop = 0, nv = 0;
+  if (!pick_rings(kp, CHI, &nop, &nv)) return cudaErrorInvalidValue;
   CUtensorMap tmV;
   memset(&tmV, 0, sizeof(tmV));
   const int useTma = ROW ? map2d(&tmV, P.V, P.N, P.F, P.ldv, TL, MT, CU_TENSOR_MAP_SWIZZLE_128B)
@@ -471,13 +615,13 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   const CUtensorMap& fa = ROW ? m.htB : m.wsB;
   const CUtensorMap& d1 = ROW ? (CHI ? m.ch1 : m.hs) : (CHI ? m.cw1 : m.wt);
   const CUtensorMap& d2 = ROW ? (CHI ? m.ch2 : m.hs) : (CHI ? m.cw2 : m.wt);
-  const WsLayout lay = ws_layout(kp, CHI, ns);
+  const WsLayout lay = ws_layout(kp, CHI, nop, nv);
   const size_t sm = 1024 + lay.total;
   const int csize = ROW ? P.tcClusterS : P.tcClusterR;
   // the cluster exchange buffers (A/B tiles, stage ring) each hold kp KB
-  if (csize > 1 && ((uint32_t)ns * lay.stage_bytes < 1024u * kp || 4 * TB < 1024u * kp)) return cudaErrorInvalidValue;
+  if (csize > 1 && lay.total - lay.op0 < 2048u * kp) return cudaErrorInvalidValue;
   // the row sweep stages its [P | Q] tile (2 x 128 x (K | 1) floats) over the stage ring and the A/B tiles
-  if (ROW && lay.total - lay.stage0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
+  if (ROW && lay.total - lay.op0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcSplitS : P.tcColTiles * P.tcSplitR);
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
@@ -497,7 +641,7 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   case BKV:                                                                                                \
     e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                              \
     if (e == cudaSuccess)                                                                                  \
-      e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, ns, P, flags, bp, \
+      e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, bp, \
                              lossPart, status);                                                            \
     break;
   switch (bp.kind) {
@@ -537,9 +681,9 @@ bool tc_build_maps(const Prob<float>& P, TcMaps* m) {
 
 int tc_ws_capacity(int kp, int csize) {
   if (kp > 64 || kp < 16) return 0;
-  const int ns = pick_stages(kp, true);
-  if (ns == 0) return 0;
-  const size_t sm = 1024 + ws_layout(kp, true, ns).total;
+  int nop = 0, nv = 0;
+  if (!pick_rings(kp, true, &nop, &nv)) return 0;
+  const size_t sm = 1024 + ws_layout(kp, true, nop, nv).total;
   auto kern = tc_ws_kernel<BK_GENERAL, true, true>;
   if (prep(kern, sm) != cudaSuccess) {
     cudaGetLastError();
