@@ -43,14 +43,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="faces", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, help="fp32 | tf32 | bf16 | fp64")
+    ap.add_argument("--precision", default=None, help="tf32 (default) | fp32 | fp64")
     ap.add_argument("--order", default="W")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--max-ttt-iters", type=int, default=1000)
+    ap.add_argument("--max-ttt-iters", type=int, default=10000)
     ap.add_argument("--no-kernel-timing", action="store_true",
-                    help="leave the library's per-kernel event timing off in the timed region")
+                    help="skip the per-kernel timing pass (no roofline, no launch count)")
     return ap.parse_args()
 
 
@@ -103,7 +103,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -171,16 +171,26 @@ def reduce_max(x, world):
     return float(t.item())
 
 
-def algorithmic_bytes(kernel, F, N, K, esize=4, S=1):
-    """Minimal DRAM bytes one launch of `kernel` must move:
-    V once, the factors it reads, the numerators/denominators or factors it writes."""
+def algorithmic_bytes(kernel, F, N, K, esize=4):
+    """Minimal DRAM bytes one launch of `kernel` must move: V once, every
+    factor-sized operand it reads once, what it writes once. Partial-sum
+    slices from splitting the streamed dimension are not counted (they are
+    the kernel's choice, not the algorithm's)."""
     V = F * N * esize
-    fac = (F * K + K * N) * esize
+    FK, KN = F * K * esize, K * N * esize
     table = {
-        "row_sweep": V + fac + 2 * F * K * esize,
-        "col_sweep": V + fac + 2 * F * K * esize + 2 * K * N * esize,
-        "tc_row_sweep": V + fac + 2 * F * K * esize,
-        "tc_col_sweep": V + fac + 2 * F * K * esize + 2 * K * N * esize,
+        # Vt tile operand (W~), the MMA1 operand (H~), the two contraction operands (H~ or chi(H)); P, Q out
+        "row_sweep": V + FK + 3 * KN + 2 * FK,
+        "tc_row_sweep": V + FK + 3 * KN + 2 * FK,
+        # H~, W~, chi(W) twice; Hn, Hd out
+        "col_sweep": V + 3 * FK + KN + 2 * KN,
+        "tc_col_sweep": V + 3 * FK + KN + 2 * KN,
+        # P, Q and W~ in; W, chi_1(W), chi_2(W) and their two tensor-core copies out
+        "rows_epilogue": 8 * FK,
+        "cols_epilogue": 8 * KN,
+        # W, H in; W~, H~ and two tensor-core copies of each out
+        "begin_iteration": 4 * (FK + KN),
+        "normalize": 2 * (FK + KN),
     }
     return table.get(kernel)
 
@@ -279,7 +289,7 @@ def run_ours(args):
     p, wl = problem(args.workload)
     beta = wl["beta"]
     F, N, K = p.shape
-    precision = args.precision or "fp32"
+    precision = args.precision or "tf32"
     esize = 8 if precision == "fp64" else 4
     dt = torch.float64 if precision == "fp64" else torch.float32
     m = NMF(F, N, K, beta, precision=precision, order=args.order)
@@ -290,52 +300,80 @@ def run_ours(args):
     m.set_factors(W, H)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        m.step_joint(1)
-    m._lib.nmf_reset_timing(m._ctx)
-    m._lib.nmf_set_timing(m._ctx, 0 if args.no_kernel_timing else 1)
+    loss_dev = torch.zeros(max(args.steps, args.warmup, 1), dtype=torch.float64, device="cuda")
+    for i in range(args.warmup):
+        m.step_joint_async(loss_dev[i:i + 1])
+    torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    losses = []
+    # Timed region: K steps enqueued back to back. Each step computes the
+    # objective into device memory (no host round trip inside the region);
+    # the L2 flush runs between steps, outside the step's events.
     with ClockSampler(local) as clk:
         for i in range(args.steps):
-            flush.fill_(float(i))                 # L2 flush between steps (not timed)
+            flush.fill_(float(i))
             starts[i].record(stream)
-            losses.append(m.step_joint(1))
+            m.step_joint_async(loss_dev[i:i + 1])
             ends[i].record(stream)
         torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - wall0
+    st = m._lib.nmf_get_status(m._ctx)
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the timed region")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
     dev_s_max = reduce_max(dev_s, world)
-    recs, launches = timing_records(m)
-    m._lib.nmf_set_timing(m._ctx, 0)
     value = world * args.steps / dev_s_max
+    losses = loss_dev[:args.steps].cpu().tolist()
+    # Kernel pass: the same steps with the library's per-kernel CUDA events on
+    # the launching stream (they add a little time per launch, so the value
+    # above comes from the untimed pass): per-kernel durations, launch counts.
+    kt_steps = 0 if args.no_kernel_timing else min(args.steps, 50)
+    recs, launches_per_step = [], None
+    if kt_steps:
+        m._lib.nmf_reset_timing(m._ctx)
+        m._lib.nmf_set_timing(m._ctx, 1)
+        for i in range(kt_steps):
+            flush.fill_(float(i))
+            m.step_joint_async(loss_dev[i:i + 1])
+        torch.cuda.synchronize()
+        recs, n_launch = timing_records(m)
+        m._lib.nmf_set_timing(m._ctx, 0)
+        launches_per_step = n_launch / kt_steps
     # dominant kernel of the step and its roofline
-    dom = max(recs, key=lambda r: r[2]) if recs else None
-    roof = None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if dom:
-        name, n, ms = dom
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def roof_of(rec):
+        name, n, ms = rec
         per_launch_s = ms / 1e3 / max(n, 1)
         ab = algorithmic_bytes(name, F, N, K, esize)
-        peak = peaks.get("hbm_gbs", 6800.0)
-        if ab:
-            ach = ab / per_launch_s / 1e9
-            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "algorithmic_bytes": ab,
-                    "avg_launch_us": per_launch_s * 1e6, "launches": n,
-                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                    "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
-    kernels = {r[0]: {"launches": r[1], "ms": round(r[2], 4)} for r in recs}
+        if not ab:
+            return None
+        ach = ab / per_launch_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "algorithmic_bytes": ab,
+                "avg_launch_us": per_launch_s * 1e6, "launches": n, "peak_source": peak_src,
+                "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
+
+    dom = max(recs, key=lambda r: r[2]) if recs else None
+    roof = roof_of(dom) if dom else None
+    kernels = {}
+    for r in recs:
+        rf = roof_of(r)
+        kernels[r[0]] = {"launches": r[1], "avg_us": round(1e3 * r[2] / max(r[1], 1), 2),
+                         "GB/s": round(rf["achieved"], 1) if rf else None,
+                         "frac": round(rf["frac"], 4) if rf else None}
+    launches = round(launches_per_step * args.steps) if launches_per_step is not None else None
     # end to end through the host-buffer C-ABI call
     Vh = torch.tensor(p.V, dtype=dt).pin_memory()
     Wh = torch.tensor(p.W0, dtype=dt).pin_memory()
@@ -365,6 +403,7 @@ def run_ours(args):
         "roofline": roof, "gpu_launches": launches, "kernels": kernels,
         "e2e": e2e, "wall_s": wall,
         "step_ms_median": statistics.median(step_ms),
+        "objective": {"first": losses[0], "last": losses[-1]},
     }
     if rank == 0:
         if not args.no_cpu_baseline:
@@ -376,7 +415,7 @@ def run_ours(args):
             line["time_to_tolerance"] = {
                 "tol": tol, "rule": "(D_prev - D)/D <= tol, max %d iterations" % args.max_ttt_iters,
                 "jmm": time_to_tolerance(p, beta, precision, "jmm", tol, args.max_ttt_iters, args.order),
-                "bmm_same_precision": time_to_tolerance(p, beta, "fp32" if precision != "fp64" else "fp64", "bmm", tol,
+                "bmm_same_precision": time_to_tolerance(p, beta, precision, "bmm", tol,
                                                         args.max_ttt_iters, args.order),
                 "bmm_fp64": time_to_tolerance(p, beta, "fp64", "bmm", tol, args.max_ttt_iters, args.order),
             }

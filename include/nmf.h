@@ -136,6 +136,18 @@ nmf_status nmf_step_joint(nmf_ctx* ctx, int32_t iters, double* loss_out);
 /* Same as nmf_step_joint for BMM (Algorithm 1). */
 nmf_status nmf_step_alternating(nmf_ctx* ctx, int32_t iters, double* loss_out);
 
+/* Asynchronous forms of nmf_step_joint / nmf_step_alternating: the same
+ * iterations and the same objective (eq. obj_fct at the iterate entering the
+ * last iteration), written to loss_dev, caller-owned DEVICE memory holding one
+ * double per problem (a batched context writes its problems' losses in
+ * order). Stream-ordered; nothing is copied to the host and nothing
+ * synchronises, so a device-side error (non-finite update, timeout) is not
+ * returned here: the next synchronising call (nmf_get_status, nmf_loss, a
+ * step with a host loss_out) reports it and restores W and H. loss_dev ==
+ * NULL -> NMF_EINVAL. */
+nmf_status nmf_step_joint_async(nmf_ctx* ctx, int32_t iters, double* loss_dev);
+nmf_status nmf_step_alternating_async(nmf_ctx* ctx, int32_t iters, double* loss_dev);
+
 /* D_beta(V + kappa | WH + kappa) at the current factors (eq. obj_fct),
  * accumulated in FP64; synchronises. */
 nmf_status nmf_loss(nmf_ctx* ctx, double* out_host);

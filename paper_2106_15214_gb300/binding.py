@@ -23,7 +23,7 @@ EXPORTS = [
     "nmf_set_csr", "nmf_set_factors", "nmf_batch_set_packed", "nmf_step_joint",
     "nmf_step_alternating", "nmf_loss", "nmf_grad", "nmf_kkt", "nmf_batch_get_losses",
     "nmf_get_status", "nmf_step_joint_host", "nmf_set_timing", "nmf_get_timing", "nmf_reset_timing",
-    "nmf_loss_noalloc", "nmf_destroy", "nmf_status_string",
+    "nmf_loss_noalloc", "nmf_step_joint_async", "nmf_step_alternating_async", "nmf_destroy", "nmf_status_string",
 ]
 
 _lib = None
@@ -55,6 +55,8 @@ def _declare(lib):
         "nmf_batch_set_packed": [P, P, P, P],
         "nmf_step_joint": [P, I32, PD],
         "nmf_step_alternating": [P, I32, PD],
+        "nmf_step_joint_async": [P, I32, P],
+        "nmf_step_alternating_async": [P, I32, P],
         "nmf_loss": [P, PD],
         "nmf_grad": [P, P, P, PD],
         "nmf_kkt": [P, PD, PD],
@@ -203,6 +205,14 @@ class NMF:
                                              ctypes.byref(loss) if want_loss else None),
               "nmf_step_alternating")
         return loss.value if want_loss else None
+
+    def step_joint_async(self, loss_dev, iters=1):
+        """Asynchronous JMM step; the loss goes to the device tensor loss_dev (float64)."""
+        check(self._lib.nmf_step_joint_async(self._ctx, int(iters), _ptr(loss_dev)), "nmf_step_joint_async")
+
+    def step_alternating_async(self, loss_dev, iters=1):
+        check(self._lib.nmf_step_alternating_async(self._ctx, int(iters), _ptr(loss_dev)),
+              "nmf_step_alternating_async")
 
     def step_joint_host(self, V_host, W_host, H_host, iters=1):
         """Host (ideally pinned) CPU tensors in, W_host/H_host updated in place."""

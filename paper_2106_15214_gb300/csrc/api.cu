@@ -669,7 +669,9 @@ nmf_status ensure_sparse(nmf_ctx* c) {
 
 // Every kernel and copy of one step call, enqueued on c->stream (no host
 // synchronisation, no allocation: the sequence can be captured into a graph).
-nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss) {
+// readback = false: the loss (when wanted) stays in d_lossOut and nothing is
+// copied to the host (asynchronous steps).
+nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss, bool readback = true) {
   if (c->sparse) {
     const bool hfirst = c->order == NMF_H_FIRST || (c->order == NMF_ORDER_AUTO && c->F[0] < c->N[0]);
     for (int it = 0; it < iters; ++it) {
@@ -684,7 +686,7 @@ nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss) {
     else NMF_TRY(run_dense<float>(c, c->pf, joint, iters, wantLoss, tc));
     if (wantLoss && !c->lossFused) NMF_TRY(finalize_loss_dense(c));
   }
-  return enqueue_readback(c, wantLoss);
+  return readback ? enqueue_readback(c, wantLoss) : NMF_OK;
 }
 
 // ---- CUDA graphs --------------------------------------------------------------
@@ -693,10 +695,11 @@ nmf_status enqueue_step(nmf_ctx* c, bool joint, int32_t iters, bool wantLoss) {
 // The caller's stream and the context stream are ordered with events, so the
 // call stays stream-ordered on the caller's stream.
 
-uint64_t step_key(const nmf_ctx* c, bool joint, int iters, bool wantLoss) {
+uint64_t step_key(const nmf_ctx* c, bool joint, int iters, bool wantLoss, bool readback) {
   uint64_t k = (uint64_t)(uint32_t)iters;
   k = k * 4 + (joint ? 1 : 0) + (wantLoss ? 2 : 0);
   k = k * 2 + (c->timer.on ? 1 : 0);
+  k = k * 2 + (readback ? 1 : 0);
   return k;
 }
 
@@ -722,7 +725,7 @@ nmf_status ensure_graph_stream(nmf_ctx* c) {
 
 // Captures enqueue_step into a graph; returns nullptr (graphs then stay off
 // for this context) if capture is not possible.
-nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t iters, bool wantLoss) {
+nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t iters, bool wantLoss, bool readback) {
   if (ensure_graph_stream(c) != NMF_OK) return nullptr;
   cudaStream_t user = c->stream;
   nmf_ctx::GraphEntry e;
@@ -733,7 +736,7 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
   c->timer.sink = &e.sink;
   cudaGraph_t graph = nullptr;
   bool ok = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  nmf_status st = ok ? enqueue_step(c, joint, iters, wantLoss) : NMF_ECUDA;
+  nmf_status st = ok ? enqueue_step(c, joint, iters, wantLoss, readback) : NMF_ECUDA;
   if (ok) ok = cudaStreamEndCapture(c->gs, &graph) == cudaSuccess && st == NMF_OK && graph;
   if (ok) ok = cudaGraphInstantiate(&e.exec, graph, 0) == cudaSuccess;
   if (graph) cudaGraphDestroy(graph);
@@ -749,19 +752,26 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
   return &c->graphs.back();
 }
 
-nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* loss_out) {
+// loss_dev != nullptr: asynchronous step; the loss goes to that device buffer.
+nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* loss_out, double* loss_dev) {
   NMF_CU(cudaEventRecord(c->evIn, c->stream));
   NMF_CU(cudaStreamWaitEvent(c->gs, c->evIn, 0));
   NMF_CU(cudaGraphLaunch(g.exec, c->gs));
   NMF_CU(cudaEventRecord(c->evOut, c->gs));
   NMF_CU(cudaStreamWaitEvent(c->stream, c->evOut, 0));
+  if (loss_dev) {
+    NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->timer.on) NMF_CU(cudaStreamSynchronize(c->gs));
+    c->timer.credit(g.sink, c->timer.on);
+    return NMF_OK;
+  }
   if (c->timer.on || wantLoss) NMF_CU(cudaStreamSynchronize(c->gs));
   c->timer.credit(g.sink, c->timer.on);
   if (!wantLoss) return NMF_OK;
   return complete_readback(c, true, loss_out);
 }
 
-nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
+nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out, double* loss_dev = nullptr) {
   if (!c || iters < 1) return NMF_EINVAL;
   if (!data_ready(c)) return NMF_ENOTREADY;
   NMF_TRY(prepare(c));
@@ -769,24 +779,29 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out) {
   const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
   if (!c->sparse && tc && (c->batched || c->prec == NMF_BF16 || tc_kp(c->K[0]) > TC_KPMAX))
     return NMF_EUNSUPPORTED;
-  const bool wantLoss = loss_out != nullptr;
+  const bool wantLoss = loss_out != nullptr || loss_dev != nullptr;
+  const bool readback = loss_dev == nullptr;
   if (c->useGraphs && c->stream != c->gs) {
-    const uint64_t key = step_key(c, joint, iters, wantLoss);
+    const uint64_t key = step_key(c, joint, iters, wantLoss, readback);
     const void* ptrs[6] = {c->V, c->W, c->H, c->Vp, c->Wp, c->Hp};
     for (auto& g : c->graphs)
       if (!std::equal(ptrs, ptrs + 6, g.ptrs)) { invalidate_graphs(c); break; }
     for (auto& g : c->graphs)
-      if (g.key == key) return replay(c, g, wantLoss, loss_out);
+      if (g.key == key) return replay(c, g, wantLoss, loss_out, loss_dev);
     bool seen = false;
     for (uint64_t k : c->seenKeys) seen = seen || k == key;
     if (seen) {
-      nmf_ctx::GraphEntry* g = capture_step(c, key, joint, iters, wantLoss);
-      if (g) return replay(c, *g, wantLoss, loss_out);
+      nmf_ctx::GraphEntry* g = capture_step(c, key, joint, iters, wantLoss, readback);
+      if (g) return replay(c, *g, wantLoss, loss_out, loss_dev);
     } else {
       c->seenKeys.push_back(key);
     }
   }
-  NMF_TRY(enqueue_step(c, joint, iters, wantLoss));
+  NMF_TRY(enqueue_step(c, joint, iters, wantLoss, readback));
+  if (loss_dev) {
+    NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
+    return NMF_OK;
+  }
   if (!wantLoss) return NMF_OK;
   NMF_CU(cudaStreamSynchronize(c->stream));
   return complete_readback(c, true, loss_out);
@@ -948,6 +963,16 @@ nmf_status nmf_step_joint(nmf_ctx* c, int32_t iters, double* loss_out) {
 
 nmf_status nmf_step_alternating(nmf_ctx* c, int32_t iters, double* loss_out) {
   return step(c, false, iters, loss_out);
+}
+
+nmf_status nmf_step_joint_async(nmf_ctx* c, int32_t iters, double* loss_dev) {
+  if (!loss_dev) return NMF_EINVAL;
+  return step(c, true, iters, nullptr, loss_dev);
+}
+
+nmf_status nmf_step_alternating_async(nmf_ctx* c, int32_t iters, double* loss_dev) {
+  if (!loss_dev) return NMF_EINVAL;
+  return step(c, false, iters, nullptr, loss_dev);
 }
 
 nmf_status nmf_loss(nmf_ctx* c, double* out_host) {

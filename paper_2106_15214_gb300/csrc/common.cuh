@@ -207,10 +207,12 @@ __device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int 
 }
 
 // Round to the nearest TF32 value (10-bit mantissa), kept in the container type.
+// Nearest value with a 10-bit mantissa, ties away from zero (the rounding of
+// cvt.rna.tf32.f32, done with integer operations; Inf and NaN unchanged).
 __device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t r = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float((u & 0x7F800000u) == 0x7F800000u ? u : r);
 }
 __device__ __forceinline__ double tf32_round(double x) { return (double)tf32_round((float)x); }
 

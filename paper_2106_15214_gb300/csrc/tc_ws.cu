@@ -56,24 +56,26 @@ constexpr int MT = 128;
 constexpr uint32_t TB = 16384;
 constexpr int EPI_WARP0 = 4;
 constexpr uint32_t EPI_THREADS = 512;
-constexpr int MAX_OP = 8;          // operand ring slots
+constexpr int MAX_OP = 8;          // per-tile operand ring slots (B of MMA2, B of MMA3)
 constexpr int MAX_V = 6;           // V ring slots
-constexpr int NVT = 4;             // TMEM buffers for Vt tiles
+constexpr int NFA = 2;             // batch slots for the B operand of MMA1
+constexpr int BT = 4;              // tiles per MMA1 batch (N = 128)
 constexpr int ETIMEOUT = 5;
 constexpr size_t SMEM_LIMIT = 227 * 1024;
-// TMEM columns (512 allocated): Vt tiles 32 b (b < 4), the A/B tiles of
-// epilogue group g at 128 + 64 g and 160 + 64 g, the accumulators at 256 and
-// 320, the A operand of MMA1 at 384 (kp <= 64 columns).
-constexpr uint32_t TM_AB = 128, TM_ACC1 = 256, TM_ACC2 = 320, TM_ONCE = 384, TM_COLS = 512;
+// TMEM columns (512 allocated): two Vt buffers of a batch of 4 tiles (tile t of
+// batch j at 128 (j & 1) + 32 (t & 3)); the epilogue overwrites each tile's
+// Vt with its A tile. The B tiles of epilogue group g at 256 + 32 g, the
+// accumulators at 320 and 384, the A operand of MMA1 at 448 (kp <= 64).
+constexpr uint32_t TM_B = 256, TM_ACC1 = 320, TM_ACC2 = 384, TM_ONCE = 448, TM_COLS = 512;
 
 // Shared memory: the A operand of MMA1 as loaded (it moves on to TMEM), a
-// ring of MMA operand slots (B of MMA1, B of MMA2, B of MMA3 for one tile)
-// and a ring of V tiles. V has its own ring because the epilogue is done with
-// it long before MMA2/3 are done with the operands.
+// double buffer of MMA1 B operands (128 streamed rows each), a ring of
+// per-tile MMA2/3 B operands and a ring of V tiles.
 struct WsLayout {
   uint32_t once;
-  uint32_t op0, op_bytes;        // operand slot s at op0 + s * op_bytes
-  uint32_t off_fa, off_d1, off_d2;
+  uint32_t fa0, fa_bytes;        // MMA1 B slot s at fa0 + s * fa_bytes
+  uint32_t op0, op_bytes;        // MMA2/3 slot s at op0 + s * op_bytes
+  uint32_t off_d2;               // second operand inside a slot
   uint32_t v0;                   // V slot s at v0 + s * TB
   uint32_t total;
 };
@@ -82,21 +84,21 @@ __host__ __device__ inline WsLayout ws_layout(int kp, bool chi, int nop, int nv)
   WsLayout L;
   const uint32_t na = (kp + 31) / 32;
   L.once = 0;
-  L.op0 = na * TB;
-  L.off_fa = 0;
-  L.off_d1 = na * (TL * 128u);
-  L.off_d2 = chi ? L.off_d1 + (uint32_t)kp * 128u : L.off_d1;
-  L.op_bytes = L.off_d1 + (uint32_t)kp * 128u * (chi ? 2u : 1u);
+  L.fa0 = na * TB;
+  L.fa_bytes = na * TB;                                   // na sub-tiles of 128 rows x 32 floats
+  L.op0 = L.fa0 + NFA * L.fa_bytes;
+  L.off_d2 = chi ? (uint32_t)kp * 128u : 0u;
+  L.op_bytes = (uint32_t)kp * 128u * (chi ? 2u : 1u);
   L.op_bytes = (L.op_bytes + 1023u) & ~1023u;
   L.v0 = L.op0 + nop * L.op_bytes;
   L.total = L.v0 + nv * TB;
   return L;
 }
 
-// Deepest rings that fit: as many V slots as leave room for >= 4 operand slots.
+// Deepest rings that fit: V slots first (down to 4), then operand slots.
 inline bool pick_rings(int kp, bool chi, int* nop, int* nv) {
-  for (int v = MAX_V; v >= 2; --v)
-    for (int o = MAX_OP; o >= (v <= 3 ? 2 : 4); --o)
+  for (int v = MAX_V; v >= 3; --v)
+    for (int o = MAX_OP; o >= (v >= 5 ? 6 : 3); --o)
       if (1024 + ws_layout(kp, chi, o, v).total + 1024 <= SMEM_LIMIT) {
         *nop = o;
         *nv = v;
@@ -123,7 +125,7 @@ __device__ __forceinline__ bool role_wait(uint64_t* bar, uint32_t parity, volati
 
 struct Bars {
   uint64_t opfull[MAX_OP], opempty[MAX_OP], vfull[MAX_V], vempty[MAX_V];
-  uint64_t tfull[NVT], tfree[NVT], abready[2], abfree[2], once, onceT, done;
+  uint64_t fafull[NFA], fafree[NFA], tfull[2], vafree[2], abready[2], abfree[2], once, onceT, done;
 };
 
 // ROW = true: row sweep (M = 128 rows f, tiles of 32 columns n).
@@ -157,11 +159,12 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   const int64_t s1 = s0 + chunk < sLim ? s0 + chunk : sLim;
   // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
   const int ntiles = (!skip && s0 < sLim) ? (int)((s1 - s0 + TL - 1) / TL) : 0;
+  const int nbatch = (ntiles + BT - 1) / BT;
   const bool wantLoss = flags & SWEEP_LOSS;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
   const uint32_t ncols = TM_COLS;
-  const uint32_t faBytes = (uint32_t)na * TL * 128u, dBytes = (uint32_t)kp * 128u;
-  const uint32_t opTx = faBytes + dBytes * (CHI ? 2u : 1u);
+  const uint32_t dBytes = (uint32_t)kp * 128u;
+  const uint32_t opTx = dBytes * (CHI ? 2u : 1u);
 
   if (tid == 0) {
     s_abort = 0;
@@ -173,11 +176,13 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
       mbar_init(&bars.vfull[s], useTma ? 1u : 32u);
       mbar_init(&bars.vempty[s], EPI_THREADS / 64);   // the 8 warps of the group that reads the tile
     }
-    for (int b = 0; b < NVT; ++b) {
-      mbar_init(&bars.tfull[b], 1u);
-      mbar_init(&bars.tfree[b], EPI_THREADS / 64);
+    for (int b = 0; b < NFA; ++b) {
+      mbar_init(&bars.fafull[b], 1u);
+      mbar_init(&bars.fafree[b], 1u);
     }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars.tfull[b], 1u);
+      mbar_init(&bars.vafree[b], 1u);
       mbar_init(&bars.abready[b], EPI_THREADS / 64);
       mbar_init(&bars.abfree[b], 1u);
     }
@@ -195,8 +200,10 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   double loss = 0.0;
 
   if (warp == 0) {
-    // ---------------- operand producer: the once tile, then a slot per tile ----------------
-    // (the warp runs the loop converged; one elected lane issues each copy)
+    // ---------------- operand producer ----------------
+    // The MMA1 A tile once; per batch of 4 tiles the MMA1 B operand (128
+    // streamed rows); per tile the MMA2/3 B operands. The warp runs the loop
+    // converged; one elected lane issues each copy.
     if (ntiles > 0) {
       if (elect_one()) {
         mbar_arrive_expect_tx(&bars.once, (uint32_t)na * TB);
@@ -206,13 +213,22 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
       uint32_t ph = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int c0 = (int)(s0 + (int64_t)t * TL);   // first streamed index of the tile
+        if ((t & (BT - 1)) == 0) {
+          const int j = t / BT, fs = j & (NFA - 1);
+          if (j >= NFA && !__all_sync(0xffffffffu, role_wait(&bars.fafree[fs], (uint32_t)((j - NFA) / NFA) & 1u, &s_abort, status)))
+            break;
+          if (elect_one()) {
+            mbar_arrive_expect_tx(&bars.fafull[fs], (uint32_t)na * TB);
+            for (int a = 0; a < na; ++a)
+              tma_load_2d(base + L.fa0 + fs * L.fa_bytes + a * TB, &tmFa, 32 * a, c0, &bars.fafull[fs]);
+          }
+          __syncwarp();
+        }
         if (t >= nop && !__all_sync(0xffffffffu, role_wait(&bars.opempty[st], ph ^ 1u, &s_abort, status))) break;
         unsigned char* sb = base + L.op0 + st * L.op_bytes;
         if (elect_one()) {
           mbar_arrive_expect_tx(&bars.opfull[st], opTx);
-          for (int a = 0; a < na; ++a)
-            tma_load_2d(sb + L.off_fa + a * (TL * 128), &tmFa, 32 * a, c0, &bars.opfull[st]);
-          tma_load_2d(sb + L.off_d1, &tmD1, c0, 0, &bars.opfull[st]);
+          tma_load_2d(sb, &tmD1, c0, 0, &bars.opfull[st]);
           if (CHI) tma_load_2d(sb + L.off_d2, &tmD2, c0, 0, &bars.opfull[st]);
         }
         __syncwarp();
@@ -265,72 +281,75 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     }
   } else if (warp == 2) {
     // ---------------- MMA issuer ----------------
-    // The warp polls both queues converged (an elected lane issues each
-    // tcgen05 instruction): MMA1 of tile t1 (Vt into TMEM buffer t1 % 4) as
-    // soon as its operand slot is loaded and the buffer is free, MMA2/3 of
-    // tile t2 as soon as the epilogue has written its A/B tiles. The A
-    // operands of all three come from TMEM, the B operands from shared
-    // memory. Descriptors are built once; an operand at byte offset o is the
-    // base descriptor plus o / 16 (the start-address field, bits 0-13, cannot
-    // carry below 256 KB).
-    const uint32_t id_v = idesc(MT, TL, kFmtTF32), id_acc = idesc(MT, kp, kFmtTF32);
+    // The warp polls two queues converged; an elected lane issues each batch:
+    //   MMA1 of batch j (Vt of 4 tiles, N = 128, into TMEM buffer j & 1) once
+    //   its B operand is loaded and MMA2/3 of batch j - 2 (which read their A
+    //   tiles from the same buffer) have completed;
+    //   MMA2/3 of tile t2 once the epilogue has written its A/B tiles and the
+    //   tile's B operands are loaded.
+    // Every A operand is read from TMEM, every B operand from shared memory.
+    // Descriptors are built once; an operand at byte offset o is the base
+    // descriptor plus o / 16 (the start-address field, bits 0-13, cannot carry
+    // below 256 KB).
+    const uint32_t id_v = idesc(MT, BT * TL, kFmtTF32), id_acc = idesc(MT, kp, kFmtTF32);
+    const uint64_t dFa = desc_sw128(smem_u32(base + L.fa0));
     const uint64_t dOp = desc_sw128(smem_u32(base + L.op0));
-    const uint32_t op16 = L.op_bytes >> 4;
-    int t1 = 0, t2 = 0, so1 = 0, so2 = 0;
-    uint32_t ph1 = 0;
+    const uint32_t fa16 = L.fa_bytes >> 4, op16 = L.op_bytes >> 4, d2_16 = L.off_d2 >> 4;
+    int j1 = 0, t2 = 0, so2 = 0;
+    uint32_t po2 = 0;
     uint64_t idle0 = 0;
     bool ok = ntiles > 0 && role_wait(&bars.onceT, 0u, &s_abort, status);
     ok = __all_sync(0xffffffffu, ok);
     fence_after_sync();
     while (ok && t2 < ntiles) {
       bool prog = false;
-      bool can1 = t1 < ntiles && mbar_test(&bars.opfull[so1], ph1) &&
-                  (t1 < NVT || mbar_test(&bars.tfree[t1 & 3], (uint32_t)((t1 - NVT) >> 2) & 1u));
+      bool can1 = j1 < nbatch && mbar_test(&bars.fafull[j1 & (NFA - 1)], (uint32_t)(j1 / NFA) & 1u) &&
+                  (j1 < 2 || mbar_test(&bars.vafree[j1 & 1], (uint32_t)((j1 - 2) >> 1) & 1u));
       can1 = __shfl_sync(0xffffffffu, can1, 0);
       if (can1) {
         fence_after_sync();
-        const uint64_t dFa = dOp + (uint64_t)(so1 * op16 + (L.off_fa >> 4));
-        const uint32_t dv = tbase + 32 * (t1 & 3);
-        // unrolled (offsets fold to constants): the MMA warp shares its
-        // scheduler with four busy epilogue warps, so every instruction counts
-        #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          if (ks < kp / 8) {
-            const uint32_t k0 = (uint32_t)ks * 8u;
-            const uint64_t db = dFa + (((k0 >> 5) * (uint32_t)(TL * 128) + (k0 & 31u) * 4u) >> 4);
-            if (elect_one()) mma_tf32_ts(dv, tbase + TM_ONCE + k0, db, id_v, ks > 0);
-          }
+        const uint64_t db0 = dFa + (uint64_t)((j1 & (NFA - 1)) * fa16);
+        const uint32_t dv = tbase + 128u * (j1 & 1);
+        if (elect_one()) {
+          #pragma unroll
+          for (int ks = 0; ks < 8; ++ks)
+            if (ks < kp / 8) {
+              const uint32_t k0 = (uint32_t)ks * 8u;
+              mma_tf32_ts(dv, tbase + TM_ONCE + k0, db0 + (((k0 >> 5) * TB + (k0 & 31u) * 4u) >> 4), id_v, ks > 0);
+            }
+          mma_commit(&bars.tfull[j1 & 1]);
+          mma_commit(&bars.fafree[j1 & (NFA - 1)]);
         }
-        if (elect_one()) mma_commit(&bars.tfull[t1 & 3]);
         __syncwarp();
-        ++t1;
-        if (++so1 == nop) {
-          so1 = 0;
-          ph1 ^= 1u;
-        }
+        ++j1;
         prog = true;
       }
-      bool can2 = t2 < t1 && mbar_test(&bars.abready[t2 & 1], (uint32_t)(t2 >> 1) & 1u);
+      bool can2 = t2 < j1 * BT && mbar_test(&bars.abready[t2 & 1], (uint32_t)(t2 >> 1) & 1u) &&
+                  mbar_test(&bars.opfull[so2], po2);
       can2 = __shfl_sync(0xffffffffu, can2, 0);
       if (can2) {
         fence_after_sync();
         const int b = t2 & 1;
-        const uint32_t tA = tbase + TM_AB + 64u * b, tB = tA + 32u;
-        const uint64_t dD1 = dOp + (uint64_t)(so2 * op16 + (L.off_d1 >> 4));
-        const uint64_t dD2 = dOp + (uint64_t)(so2 * op16 + (L.off_d2 >> 4));
-        #pragma unroll
-        for (int ks = 0; ks < TL / 8; ++ks) {
-          const uint32_t acc = (t2 > 0 || ks > 0) ? 1u : 0u;
-          if (elect_one()) mma_tf32_ts(t_acc1, tA + 8u * ks, dD1 + 2u * ks, id_acc, acc);   // 32 bytes along K
-          if (elect_one()) mma_tf32_ts(t_acc2, tB + 8u * ks, dD2 + 2u * ks, id_acc, acc);
-        }
+        const uint32_t tA = tbase + 128u * ((t2 >> 2) & 1) + 32u * (t2 & 3), tB = tbase + TM_B + 32u * b;
+        const uint64_t dD1 = dOp + (uint64_t)(so2 * op16), dD2 = dD1 + d2_16;
+        const bool lastOfBatch = (t2 & (BT - 1)) == BT - 1 || t2 == ntiles - 1;
         if (elect_one()) {
+          #pragma unroll
+          for (int ks = 0; ks < TL / 8; ++ks) {
+            const uint32_t acc = (t2 > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32_ts(t_acc1, tA + 8u * ks, dD1 + 2u * ks, id_acc, acc);   // 32 bytes along K
+            mma_tf32_ts(t_acc2, tB + 8u * ks, dD2 + 2u * ks, id_acc, acc);
+          }
           mma_commit(&bars.abfree[b]);
           mma_commit(&bars.opempty[so2]);
+          if (lastOfBatch) mma_commit(&bars.vafree[(t2 >> 2) & 1]);
         }
         __syncwarp();
         ++t2;
-        if (++so2 == nop) so2 = 0;
+        if (++so2 == nop) {
+          so2 = 0;
+          po2 ^= 1u;
+        }
         prog = true;
       }
       if (prog) {
@@ -356,9 +375,10 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   } else if (warp >= EPI_WARP0) {
     // ---------------- epilogue ----------------
     // Two groups of 8 warps take alternate tiles (group g: tiles g, g + 2, ...;
-    // A/B buffer g), so one group's waits overlap the other's work. Within a
-    // group, warp (q4, half) owns TMEM lanes 32 q4 .. 32 q4 + 31 and streamed
-    // indices 16 half .. 16 half + 15.
+    // TMEM B buffer g), so one group's waits overlap the other's work. Within
+    // a group, warp (q4, half) owns TMEM lanes 32 q4 .. 32 q4 + 31 and
+    // streamed indices 16 half .. 16 half + 15 of the tile. A replaces the
+    // tile's Vt in TMEM (each thread rewrites the columns it read).
     const int ew = warp - EPI_WARP0;
     const int q4 = warp & 3;
     const int g = (ew >> 2) & 1, half = ew >> 3;
@@ -368,7 +388,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     const bool mvalid = gm < mLim;
     const int jb0 = 16 * half;
     const float beta = (float)bp.beta;
-    const uint32_t tA = tbase + TM_AB + 64u * g + lane_off + jb0, tB = tA + 32u;
+    const uint32_t tBg = tbase + TM_B + 32u * g + lane_off + jb0;
     if (ew < 4 && ntiles > 0) {
       // warps 4-7 move the A operand of MMA1 (row mrow, kp columns) from shared memory to TMEM
       if (__all_sync(0xffffffffu, role_wait(&bars.once, 0u, &s_abort, status))) {
@@ -391,15 +411,15 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     int sv = g;                                               // nv >= 2: tile g sits in V slot g, phase 0
     uint32_t pv = 0;
     for (int t = g; t < ntiles; t += 2) {
-      const int tb = t & 3;
       const int64_t c0 = s0 + (int64_t)t * TL;
       const int nvalid = (int)((s1 - c0) < TL ? (s1 - c0) : TL);   // streamed indices of this tile inside the chunk
-      // waits decided warp-wide (the warp arrives once and tcgen05.ld is warp-wide)
-      if (!__all_sync(0xffffffffu, role_wait(&bars.tfull[tb], (uint32_t)(t >> 2) & 1u, &s_abort, status))) break;
+      const uint32_t tV = tbase + 128u * ((t >> 2) & 1) + 32u * (t & 3) + lane_off + jb0;
+      // waits decided warp-wide (the warp arrives once and tcgen05.ld/st are warp-wide)
+      if (!__all_sync(0xffffffffu, role_wait(&bars.tfull[(t >> 2) & 1], (uint32_t)(t >> 3) & 1u, &s_abort, status))) break;
       if (!__all_sync(0xffffffffu, role_wait(&bars.vfull[sv], pv, &s_abort, status))) break;
       fence_after_sync();
       float vt[16];
-      tmem_ld16(tbase + 32 * tb + lane_off + jb0, vt);
+      tmem_ld16(tV, vt);
       const unsigned char* vb = base + L.v0 + sv * TB;
       float vv[16];
       if (ROW) {
@@ -414,12 +434,8 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
         for (int j = 0; j < 16; ++j) vv[j] = Vs[(jb0 + j) * MT];
       }
       tmem_ld_wait();
-      fence_before_sync();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&bars.tfree[tb]);
-        mbar_arrive(&bars.vempty[sv]);
-      }
+      if (lane == 0) mbar_arrive(&bars.vempty[sv]);
       if (t >= 2 && !__all_sync(0xffffffffu, role_wait(&bars.abfree[g], (uint32_t)((t - 2) >> 1) & 1u, &s_abort, status)))
         break;
       float tl = 0.f;
@@ -447,8 +463,8 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
         vv[j] = to_tf32(vv[j]);
         vt[j] = to_tf32(vt[j]);
       }
-      tmem_st16(tA, vv);
-      tmem_st16(tB, vt);
+      tmem_st16(tV, vv);                               // A over this tile's Vt
+      tmem_st16(tBg, vt);
       if (wantLoss) loss += (double)tl;
       tmem_st_wait();
       fence_before_sync();
@@ -494,7 +510,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     cluster_sync();
     int round = 0;
     for (int stp = 1; stp < csize; stp <<= 1, ++round) {
-      unsigned char* buf = base + L.op0 + ((round & 1) ? 1024u * kp : 0u);
+      unsigned char* buf = base + L.fa0 + ((round & 1) ? 1024u * kp : 0u);
       const uint32_t qbase = (uint32_t)((isQ ? per * 2 : 0) + col0) / 4;   // this thread's first float4
       if (epi && (rank & (2 * stp - 1)) == (uint32_t)stp) {
         const uint32_t remote = dsmem_map(buf, rank - stp);
@@ -520,7 +536,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
     // (row-major F x K): stage them in shared memory (odd row stride, no bank
     // conflicts) and let the whole block write them out coalesced.
     const int Ks = K | 1;
-    float* stg = reinterpret_cast<float*>(base + L.op0);   // rings idle: MMAs done, exchange over
+    float* stg = reinterpret_cast<float*>(base + L.fa0);   // rings idle: MMAs done, exchange over
     __syncthreads();
     if (epi && sl % csize == 0) {
       float* row = stg + (isQ ? MT * Ks : 0) + mrow * Ks + col0;
@@ -619,9 +635,9 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   const size_t sm = 1024 + lay.total;
   const int csize = ROW ? P.tcClusterS : P.tcClusterR;
   // the cluster exchange buffers (A/B tiles, stage ring) each hold kp KB
-  if (csize > 1 && lay.total - lay.op0 < 2048u * kp) return cudaErrorInvalidValue;
+  if (csize > 1 && lay.total - lay.fa0 < 2048u * kp) return cudaErrorInvalidValue;
   // the row sweep stages its [P | Q] tile (2 x 128 x (K | 1) floats) over the stage ring and the A/B tiles
-  if (ROW && lay.total - lay.op0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
+  if (ROW && lay.total - lay.fa0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcSplitS : P.tcColTiles * P.tcSplitR);
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
@@ -666,9 +682,9 @@ bool tc_build_maps(const Prob<float>& P, TcMaps* m) {
   const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
   bool ok = true;
   ok = ok && map2d(&m->wsA, P.sWS, ks, F, ks, 32, MT, SW);
-  ok = ok && map2d(&m->wsB, P.sWS, ks, F, ks, 32, TL, SW);
+  ok = ok && map2d(&m->wsB, P.sWS, ks, F, ks, 32, BT * TL, SW);
   ok = ok && map2d(&m->htA, P.sHT, ks, N, ks, 32, MT, SW);
-  ok = ok && map2d(&m->htB, P.sHT, ks, N, ks, 32, TL, SW);
+  ok = ok && map2d(&m->htB, P.sHT, ks, N, ks, 32, BT * TL, SW);
   ok = ok && map2d(&m->hs, P.sHS, N, kp, P.Np, 32, kp, SW);
   ok = ok && map2d(&m->ch1, P.sCH1, N, kp, P.Np, 32, kp, SW);
   ok = ok && map2d(&m->ch2, P.sCH2, N, kp, P.Np, 32, kp, SW);

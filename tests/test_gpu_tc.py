@@ -134,3 +134,39 @@ def test_tf32_cluster_reduction(lib, monkeypatch, cluster, K, method, order):
     monkeypatch.delenv("NMF_TC_CLUSTER")
     W1, H1, _, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
     assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
+
+
+@pytest.mark.parametrize("prec,method", [("tf32", "jmm"), ("fp32", "bmm"), ("fp64", "jmm")])
+def test_async_step_matches_sync(lib, prec, method):
+    """nmf_step_*_async computes the same iterates and objective as the
+    synchronous call (bitwise: same kernels, same order), leaving the loss in
+    device memory; nmf_get_status then reports OK."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    V, W0, H0 = problem(257, 331, 20, seed=8)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    outs = []
+    for mode in ("sync", "async"):
+        m = NMF(257, 331, 20, 1.0, precision=prec, order="H")
+        Vd = torch.tensor(V, dtype=dt, device="cuda")
+        Wd = torch.tensor(W0, dtype=dt, device="cuda")
+        Hd = torch.tensor(H0, dtype=dt, device="cuda")
+        m.set_dense(Vd)
+        m.set_factors(Wd, Hd)
+        losses = []
+        if mode == "sync":
+            for _ in range(4):
+                losses.append(m.step_joint(1) if method == "jmm" else m.step_alternating(1))
+        else:
+            buf = torch.zeros(4, dtype=torch.float64, device="cuda")
+            for i in range(4):
+                if method == "jmm":
+                    m.step_joint_async(buf[i:i + 1])
+                else:
+                    m.step_alternating_async(buf[i:i + 1])
+            assert lib.nmf_get_status(m._ctx) == 0
+            losses = buf.cpu().tolist()
+        outs.append((Wd.cpu().numpy(), Hd.cpu().numpy(), losses))
+    (W1, H1, l1), (W2, H2, l2) = outs
+    assert np.array_equal(W1, W2) and np.array_equal(H1, H2)
+    assert l1 == l2
