@@ -519,7 +519,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     f.lossPart = lp;
     f.lossBlocks = lossFromRow ? rowGrid : colGrid;
     f.lossOut = c->d_lossOut;
-    f.normPart = c->d_normPart;
+    f.normPart = static_cast<void*>(c->d_normPart);
     f.counter = c->d_counter;
     return f;
   };
@@ -542,7 +542,13 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     const bool lossHere = wantLoss && it == iters - 1;
     const int CL = C | (lossHere ? SWEEP_LOSS : 0);
     const int lossFlag = (fuse && lossHere) ? FUSE_LOSS : 0;
-    NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
+    if (tci && c->count == 1 && c->hpf[0].sWS) {
+      if constexpr (std::is_same<T, float>::value)
+        NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
+                     [&] { return launch_tc_copies<float>(c->hpf[0], true, true, true, status, st); }));
+    } else {
+      NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
+    }
     bool normDone = false;
     if (joint) {
       for (int l = 1; l <= L; ++l) {

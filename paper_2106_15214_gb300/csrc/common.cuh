@@ -259,6 +259,18 @@ template <> struct DB<float> {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. The step's kernels are launched with the
+// programmatic-serialization attribute, so a kernel's blocks may be scheduled
+// while its predecessor in the stream is still finishing. pdl_wait() returns
+// once that predecessor has completed and its writes are visible (a no-op for
+// a normal launch); every such kernel calls it before it touches anything a
+// predecessor wrote (the status word included). pdl_trigger() lets the next
+// kernel be scheduled as soon as every block of this one has started.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------
 

@@ -3,6 +3,8 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstring>
 #include <stdint.h>
 
 #include <mutex>
@@ -154,7 +156,7 @@ struct EpiFuse {
   const double* lossPart = nullptr;
   int lossBlocks = 0;
   double* lossOut = nullptr;
-  double* normPart = nullptr;   // [W epilogue blocks][K]
+  void* normPart = nullptr;     // [K][W epilogue blocks], element type T
   unsigned* counter = nullptr;  // zero between launches
 };
 
@@ -179,6 +181,28 @@ inline int rows_epilogue_grid(int totW, int G) { return (int)(((int64_t)totW * E
 template <typename T>
 inline int rows_epilogue_lanes(const Plan<T>& pl, int tc) {
   return pl.count == 1 ? rows_epilogue_lanes_host(1, pl.rowSlices[tc ? 1 : 0]) : 1;
+}
+// Tensor-core copies (TF32 shadows) of W and/or H of one problem, and with
+// `tilde` the W~, H~ copies too (the begin of a tensor-core iteration).
+template <typename T>
+cudaError_t launch_tc_copies(const Prob<T>& P, bool doW, bool doH, bool tilde, const int* status, cudaStream_t st);
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()
+// before reading anything its predecessor wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 // Copies W -> Wt and H -> Ht for every problem (skipped once status is set).
 template <typename T>

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(NT)
 row_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                  int wsel, int hsel, int dsel, int flags, BetaParams bp,
                  double* __restrict__ lossPart, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   const int b = blockIdx.x;
   const int pi = find_problem(prefix, count, b);
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(NT)
 col_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                  int wsel, int hsel, int csel, int flags, BetaParams bp,
                  double* __restrict__ lossPart, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   const int b = blockIdx.x;
   const int pi = find_problem(prefix, count, b);
@@ -277,9 +281,8 @@ __device__ __forceinline__ void sum_slices(const T* __restrict__ part, int64_t s
 // sums of squares, and / or the objective from the sweep's loss partials.
 template <typename T>
 __device__ __forceinline__ void last_block_finalize(const EpiFuse& fz, const Prob<T>& P, int nblocks,
-                                                    double* sbuf /* blockDim.x doubles, for FUSE_NORM_PART */) {
+                                                    T* sbuf /* blockDim.x values, for FUSE_NORM_PART */) {
   __shared__ bool s_last;
-  __shared__ double red[32];
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -289,19 +292,23 @@ __device__ __forceinline__ void last_block_finalize(const EpiFuse& fz, const Pro
   if (!s_last) return;
   __threadfence();
   if (fz.flags & FUSE_NORM_PART) {
-    // R threads per column: thread (k, j) sums the partials of blocks j, j + R,
-    // ... with eight loads in flight, then thread k adds its R sums in order
-    // (deterministic; one L2 round trip covers 8 R blocks).
+    // Partials are [k][block] in the context's precision (a column norm needs
+    // no FP64; FP64 issues at a small fraction of the FP32 rate here). R
+    // threads per column: thread (k, j) sums blocks j, j + R, ... (coalesced
+    // over j, eight loads in flight), then thread k adds its R sums in order:
+    // deterministic.
     const int t = threadIdx.x, R = blockDim.x / P.K;
-    double sq = 0.0;
+    const T* part = static_cast<const T*>(fz.normPart);
+    T sq = T(0);
     if (t < R * P.K) {
       const int k = t / R, j = t - k * R;
+      const T* row = part + (int64_t)k * nblocks;
       for (int b0 = j; b0 < nblocks; b0 += 8 * R) {
-        double v[8];
+        T v[8];
         #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int bb = b0 + u * R;
-          v[u] = bb < nblocks ? __ldcg(&fz.normPart[(int64_t)bb * P.K + k]) : 0.0;
+          v[u] = bb < nblocks ? __ldcg(&row[bb]) : T(0);
         }
         #pragma unroll
         for (int u = 0; u < 8; ++u) sq += v[u];
@@ -310,15 +317,16 @@ __device__ __forceinline__ void last_block_finalize(const EpiFuse& fz, const Pro
     sbuf[t] = sq;
     __syncthreads();
     if (t < P.K) {
-      double sum = 0.0;
+      T sum = T(0);
       for (int j = 0; j < R; ++j) sum += sbuf[t * R + j];
-      P.norms[t] = (T)sqrt(sum);
+      P.norms[t] = sqrt(sum);
     }
   }
-  if (fz.flags & FUSE_LOSS) {
+  if ((fz.flags & FUSE_LOSS) && threadIdx.x < 32) {
+    // the objective in FP64, by one warp: a few partials per lane, one butterfly
     double sl = 0.0;
-    for (int b = threadIdx.x; b < fz.lossBlocks; b += blockDim.x) sl += __ldcg(&fz.lossPart[b]);
-    sl = block_sum(sl, red);
+    for (int b = threadIdx.x; b < fz.lossBlocks; b += 32) sl += __ldcg(&fz.lossPart[b]);
+    sl = warp_sum(sl);
     if (threadIdx.x == 0) fz.lossOut[0] = sl;
   }
   if (threadIdx.x == 0) *fz.counter = 0u;
@@ -335,11 +343,13 @@ __global__ void __launch_bounds__(NTH)
 rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
                      int* __restrict__ status, int tc, EpiFuse fz, int G) {
+  pdl_trigger();
+  pdl_wait();
   // With fusion every block must reach the completion counter, so a set status
   // word only skips the arithmetic.
   const bool skip = *status != 0;
   if (skip && !fz.flags) return;
-  __shared__ double s_sq[NTH];
+  __shared__ T s_sq[NTH];
   // G lanes per entry (single problem): lane j sums slices j, j + G, ... and a
   // fixed butterfly combines them; G = 1 for batched contexts.
   const int epb = NTH / G;                                 // entries per block
@@ -373,7 +383,7 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     num += __shfl_xor_sync(0xffffffffu, num, o);
     den += __shfl_xor_sync(0xffffffffu, den, o);
   }
-  double sq = 0.0;
+  T sq = T(0);
   if (inside && sub == 0) {
     if (mode == EPI_GRAD) {
       gout[idx] = den - num;
@@ -382,7 +392,7 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
       const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
       if (!isfinite(x)) atomicExch(status, 4);
       P.W[idx] = x;
-      sq = (double)x * (double)x;
+      sq = x * x;
       if (want_chi) {
         T c1, c2;
         chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
@@ -404,9 +414,9 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     for (int k = threadIdx.x; k < P.K; k += NTH) {
       // entries of column k inside this block, summed in index order
       int i = (int)(((int64_t)k - first % P.K + P.K) % P.K);
-      double acc = 0.0;
+      T acc = T(0);
       for (; i < epb && first + i < FK; i += P.K) acc += s_sq[i * G];
-      fz.normPart[(int64_t)b * P.K + k] = acc;
+      static_cast<T*>(fz.normPart)[(int64_t)k * gridDim.x + b] = acc;
     }
   }
   last_block_finalize<T>(fz, P, gridDim.x, s_sq);
@@ -421,6 +431,8 @@ __global__ void __launch_bounds__(EW)
 cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
                      int* __restrict__ status, int tc, EpiFuse fz, int totH) {
+  pdl_trigger();
+  pdl_wait();
   const bool skip = *status != 0;
   if (skip && !(fz.flags & FUSE_LOSS)) return;
   const int b = blockIdx.x;
@@ -473,6 +485,8 @@ template <typename T>
 __global__ void __launch_bounds__(EW)
 begin_iteration_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefW,
                        int totW, const int* __restrict__ prefH, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   int b = blockIdx.x;
   if (b < totW) {
@@ -510,6 +524,8 @@ template <typename T>
 __global__ void __launch_bounds__(EW)
 colnorm_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefK,
                const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   __shared__ double red[32];
   const int b = blockIdx.x;
@@ -529,6 +545,8 @@ template <typename T>
 __global__ void __launch_bounds__(EW)
 normalize_apply_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefW,
                        int totW, const int* __restrict__ prefH, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   int b = blockIdx.x;
   if (b < totW) {
@@ -556,6 +574,8 @@ normalize_apply_kernel(const Prob<T>* __restrict__ probs, int count, const int* 
 template <typename T>
 __global__ void __launch_bounds__(EW)
 shadow_factors_kernel(Prob<T> P, int which, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
   if (*status) return;
   const int64_t FK = P.F * P.K, KN = (int64_t)P.K * P.N;
   const int64_t lo = (which & 1) ? 0 : FK, hi = (which & 2) ? FK + KN : FK;
@@ -574,18 +594,72 @@ shadow_factors_kernel(Prob<T> P, int which, const int* __restrict__ status) {
   }
 }
 
+// Tensor-core copies of the factors for one problem, written coalesced.
+// Blocks [0, wBlocks) take EW entries of W each (W~ copy when `tilde`, then the
+// TF32 copies sWS (F x ks) and sWT (K x Fp)); block wBlocks + b takes columns
+// [32 b, 32 b + 32) of H, all K rows: read along n, H~ and sHS (K x Np) written
+// along n, sHT (N x ks) written along k after a transpose in shared memory
+// (a direct transposed store would put every element in its own sector).
+template <typename T>
+__global__ void __launch_bounds__(EW)
+tc_copies_kernel(Prob<T> P, int wBlocks, int doW, int doH, int tilde, const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
+  if (*status) return;
+  __shared__ float tile[32][KMAX + 1];
+  if ((int)blockIdx.x < wBlocks) {
+    if (!doW) return;
+    const int64_t idx = (int64_t)blockIdx.x * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const T w = P.W[idx];
+      if (tilde) P.Wt[idx] = w;
+      const int64_t f = idx / P.K, k = idx - f * P.K;
+      const float r = tf32_round((float)w);
+      P.sWS[f * P.ks + k] = (T)r;
+      P.sWT[k * P.Fp + f] = (T)r;
+    }
+    return;
+  }
+  if (!doH) return;
+  const int64_t n0 = (int64_t)(blockIdx.x - wBlocks) * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = n0 + lane;
+  for (int k = w; k < P.K; k += EW / 32) {
+    if (n < P.N) {
+      const T h = P.H[(int64_t)k * P.N + n];
+      if (tilde) P.Ht[(int64_t)k * P.N + n] = h;
+      const float r = tf32_round((float)h);
+      P.sHS[(int64_t)k * P.Np + n] = (T)r;
+      tile[lane][k] = r;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * P.K; i += EW) {
+    const int nl = i / P.K, k = i - nl * P.K;
+    if (n0 + nl < P.N) P.sHT[(n0 + nl) * P.ks + k] = (T)tile[nl][k];
+  }
+}
+
+template <typename T>
+cudaError_t launch_tc_copies(const Prob<T>& P, bool doW, bool doH, bool tilde, const int* status, cudaStream_t st) {
+  const int wBlocks = doW ? (int)((P.F * P.K + EW - 1) / EW) : 0;
+  const int hBlocks = doH ? (int)((P.N + 31) / 32) : 0;
+  if (wBlocks + hBlocks == 0) return cudaSuccess;
+  return launch_pdl(tc_copies_kernel<T>, dim3(wBlocks + hBlocks), dim3(EW), 0, st, P, wBlocks, doW ? 1 : 0, doH ? 1 : 0,
+                    tilde ? 1 : 0, status);
+}
+
 template <typename T>
 cudaError_t launch_shadow_factors(const Prob<T>& P, int which, const int* status, cudaStream_t st) {
-  const int64_t n = ((which & 1) ? P.F * P.K : 0) + ((which & 2) ? (int64_t)P.K * P.N : 0);
-  const unsigned grid = (unsigned)std::min<int64_t>(2048, (n + EW - 1) / EW);
-  shadow_factors_kernel<T><<<grid > 0 ? grid : 1, EW, 0, st>>>(P, which, status);
-  return cudaGetLastError();
+  return launch_tc_copies<T>(P, (which & 1) != 0, (which & 2) != 0, false, status, st);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(EW)
 kkt_kernel(const T* __restrict__ W, const T* __restrict__ gW, int64_t nW, const T* __restrict__ H,
            const T* __restrict__ gH, int64_t nH, double* __restrict__ out) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double red[32];
   double sw = 0.0, sh = 0.0;
   for (int64_t i = threadIdx.x; i < nW; i += EW) sw += fabs((double)min(W[i], gW[i]));
@@ -622,8 +696,10 @@ cudaError_t row_sweep_bk_kj(const Plan<T>& pl, int wsel, int hsel, int dsel, int
   const size_t sm = row_smem_bytes<T>(pl.maxK, dsel);
   cudaError_t e = prep_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<pl.totRow, NT, sm, st>>>(pl.d_probs, pl.count, pl.d_prefRow, wsel, hsel, dsel, flags, bp,
-                                  lossPart, status);
+  {
+    const cudaError_t le_ = launch_pdl(kern, dim3(pl.totRow), dim3(NT), sm, st, pl.d_probs, pl.count, pl.d_prefRow, wsel, hsel, dsel, flags, bp, lossPart, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
@@ -643,8 +719,10 @@ cudaError_t col_sweep_bk_kj(const Plan<T>& pl, int wsel, int hsel, int csel, int
   const size_t sm = col_smem_bytes<T>(pl.maxK, csel);
   cudaError_t e = prep_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<pl.totCol, NT, sm, st>>>(pl.d_probs, pl.count, pl.d_prefCol, wsel, hsel, csel, flags, bp,
-                                  lossPart, status);
+  {
+    const cudaError_t le_ = launch_pdl(kern, dim3(pl.totCol), dim3(NT), sm, st, pl.d_probs, pl.count, pl.d_prefCol, wsel, hsel, csel, flags, bp, lossPart, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
@@ -685,19 +763,25 @@ cudaError_t rows_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
                         const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc, const EpiFuse& fz) {
   const int G = rows_epilogue_lanes(pl, tc);
   if (pl.count == 1)
-    rows_epilogue_kernel<T, BK, 1024><<<rows_epilogue_grid(pl.totW, G), 1024, 0, st>>>(
-        pl.d_probs, pl.count, pl.d_prefW, mode, basesel, want_chi, bp, gout, status, tc, fz, G);
+    {
+      const cudaError_t le_ = launch_pdl(rows_epilogue_kernel<T, BK, 1024>, dim3(rows_epilogue_grid(pl.totW, G)), dim3(1024), 0, st, pl.d_probs, pl.count, pl.d_prefW, mode, basesel, want_chi, bp, gout, status, tc, fz, G);
+      if (le_ != cudaSuccess) return le_;
+    }
   else
-    rows_epilogue_kernel<T, BK, EW><<<pl.totW, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, mode,
-                                                            basesel, want_chi, bp, gout, status, tc, fz, 1);
+    {
+      const cudaError_t le_ = launch_pdl(rows_epilogue_kernel<T, BK, EW>, dim3(pl.totW), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, mode, basesel, want_chi, bp, gout, status, tc, fz, 1);
+      if (le_ != cudaSuccess) return le_;
+    }
   return cudaGetLastError();
 }
 template <typename T, int BK>
 cudaError_t cols_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
                         const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc, const EpiFuse& fz) {
   const int grid = pl.totH + ((fz.flags & FUSE_NORM_APPLY) ? pl.totW : 0);
-  cols_epilogue_kernel<T, BK><<<grid, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefH, mode,
-                                                   basesel, want_chi, bp, gout, status, tc, fz, pl.totH);
+  {
+    const cudaError_t le_ = launch_pdl(cols_epilogue_kernel<T, BK>, dim3(grid), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefH, mode, basesel, want_chi, bp, gout, status, tc, fz, pl.totH);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
@@ -717,32 +801,44 @@ cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int w
 // W /= norms, H *= norms from P.norms (the norms a fused W epilogue produced).
 template <typename T>
 cudaError_t launch_normalize_apply(const Plan<T>& pl, const int* status, cudaStream_t st) {
-  normalize_apply_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
-                                                               pl.totW, pl.d_prefH, status);
+  {
+    const cudaError_t le_ = launch_pdl(normalize_apply_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, pl.totW, pl.d_prefH, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st) {
-  begin_iteration_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
-                                                               pl.totW, pl.d_prefH, status);
+  {
+    const cudaError_t le_ = launch_pdl(begin_iteration_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, pl.totW, pl.d_prefH, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_normalize(const Plan<T>& pl, const int* status, cudaStream_t st) {
-  colnorm_kernel<T><<<pl.totK, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefK, status);
+  {
+    const cudaError_t le_ = launch_pdl(colnorm_kernel<T>, dim3(pl.totK), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefK, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  normalize_apply_kernel<T><<<pl.totW + pl.totH, EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW,
-                                                               pl.totW, pl.d_prefH, status);
+  {
+    const cudaError_t le_ = launch_pdl(normalize_apply_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, pl.totW, pl.d_prefH, status);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T* gH, int64_t nH,
                        double* out, cudaStream_t st) {
-  kkt_kernel<T><<<1, EW, 0, st>>>(W, gW, nW, H, gH, nH, out);
+  {
+    const cudaError_t le_ = launch_pdl(kkt_kernel<T>, dim3(1), dim3(EW), 0, st, W, gW, nW, H, gH, nH, out);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
@@ -757,6 +853,7 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
                                                T*, int*, cudaStream_t, int, const EpiFuse&);       \
   template cudaError_t launch_normalize_apply<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
+  template cudaError_t launch_tc_copies<T>(const Prob<T>&, bool, bool, bool, const int*, cudaStream_t); \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \
                                      double*, cudaStream_t);                                       \

@@ -136,7 +136,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
              const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
              const __grid_constant__ CUtensorMap tmD2, int useTma, int nop, int nv, Prob<float> P, int flags,
              BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
-  const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
+  pdl_trigger();
   extern __shared__ unsigned char smem_raw[];
   __shared__ Bars bars;
   __shared__ uint32_t tslot;
@@ -158,8 +158,7 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   const int64_t s0 = (int64_t)sl * chunk;
   const int64_t s1 = s0 + chunk < sLim ? s0 + chunk : sLim;
   // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
-  const int ntiles = (!skip && s0 < sLim) ? (int)((s1 - s0 + TL - 1) / TL) : 0;
-  const int nbatch = (ntiles + BT - 1) / BT;
+  const int ntilesGeom = s0 < sLim ? (int)((s1 - s0 + TL - 1) / TL) : 0;
   const bool wantLoss = flags & SWEEP_LOSS;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
   const uint32_t ncols = TM_COLS;
@@ -195,6 +194,12 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
+  // everything above overlaps the previous kernel's tail; from here on its
+  // writes (the factor copies, the status word) are visible
+  pdl_wait();
+  const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
+  const int ntiles = skip ? 0 : ntilesGeom;
+  const int nbatch = (ntiles + BT - 1) / BT;
   const uint32_t tbase = tslot;
   const uint32_t t_acc1 = tbase + TM_ACC1, t_acc2 = tbase + TM_ACC2;   // P | Hn, Q | Hd
   double loss = 0.0;
@@ -645,13 +650,15 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   cfg.blockDim = dim3(WS_THREADS);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaError_t e = cudaSuccess;
 #define NMF_WS_CASE(BKV)                                                                                   \
   case BKV:                                                                                                \
