@@ -350,8 +350,9 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max(tcRowGrid, tcColGrid));
   NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
   if (!c->batched) {
-    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_normPart),
-                   sizeof(double) * (size_t)rows_epilogue_grid(pl.totW, ROWS_EPI_MAX_LANES) * c->K[0]));
+    // W-epilogue norm partials ([K][blocks]), or [K][SMs] for the persistent step kernel
+    const size_t normParts = std::max<size_t>((size_t)rows_epilogue_grid(pl.totW, ROWS_EPI_MAX_LANES), (size_t)c->sms);
+    NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_normPart), sizeof(double) * normParts * c->K[0]));
     NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_counter), 256));
     NMF_CU(cudaMemset(c->d_counter, 0, 256));
   }
@@ -538,6 +539,32 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     return basesel == SEL_CUR ? shadows(2) : NMF_OK;
   };
   const bool norm = c->normalize != 0;
+  // NMF_TC_STEP=1: one persistent cooperative launch per iteration
+  // (tc_step.cu) where it applies. Off by default: on the 361 x 2429 and
+  // 513 x 20000 workloads it measured slower than the per-kernel sequence
+  // below with programmatic dependent launch (the sweeps' pipeline fill no
+  // longer overlaps the previous phase, and the cooperative launch costs more).
+  if constexpr (std::is_same<T, float>::value) {
+    const char* stepEnv = std::getenv("NMF_TC_STEP");
+    const bool stepOn = stepEnv && stepEnv[0] == '1';
+    if (tc && stepOn && joint && L == 1 && norm && fuse && c->count == 1 &&
+        tc_step_supported(c->hpf[0], c->tcmaps, c->sms)) {
+      for (int it = 0; it < iters; ++it) {
+        TcStepArgs a;
+        a.wfirst = wfirst;
+        a.wantLoss = wantLoss && it == iters - 1;
+        a.lossPart = lp;
+        a.lossOut = c->d_lossOut;
+        a.normPart = reinterpret_cast<float*>(c->d_normPart);
+        a.gridBar = c->d_counter + 16;
+        a.status = status;
+        NMF_CU(timed(&c->timer, st, "tc_step", 1,
+                     [&] { return launch_tc_step(c->hpf[0], c->tcmaps, bp, a, c->sms, st); }));
+      }
+      c->lossFused = true;
+      return NMF_OK;
+    }
+  }
   for (int it = 0; it < iters; ++it) {
     const bool lossHere = wantLoss && it == iters - 1;
     const int CL = C | (lossHere ? SWEEP_LOSS : 0);

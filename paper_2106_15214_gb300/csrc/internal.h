@@ -237,6 +237,29 @@ struct TcMaps {
   bool ok = false;
 };
 bool tc_build_maps(const Prob<float>& P, TcMaps* m);
+// Tensor map of V for the row (row = true) or column sweep; false when V
+// cannot be addressed by TMA (the kernels then load V with cp.async).
+bool tc_map_v(const Prob<float>& P, bool row, CUtensorMap* m);
+// Ring depths and dynamic shared memory of the warp-specialised sweep.
+bool tc_ws_rings(int kp, bool chi, int* nop, int* nv, size_t* smem);
+
+// One JMM outer iteration (L = 1, normalisation on) of a single dense TF32
+// problem in one persistent cooperative launch (tc_step.cu): the factor
+// copies, both sweeps, both epilogues and the normalisation as phases
+// separated by grid barriers. False when the context does not qualify
+// (the caller then runs the per-kernel sequence).
+struct TcStepArgs {
+  bool wfirst;
+  bool wantLoss;
+  double* lossPart;
+  double* lossOut;
+  float* normPart;      // [K][blocks]
+  unsigned* gridBar;    // two words, zero between launches
+  int* status;
+};
+bool tc_step_supported(const Prob<float>& P, const TcMaps& m, int sms);
+cudaError_t launch_tc_step(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, const TcStepArgs& a,
+                           int sms, cudaStream_t st);
 
 cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int dsel, int flags,
                                 bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);

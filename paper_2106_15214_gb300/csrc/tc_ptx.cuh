@@ -98,6 +98,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 }
 
 // ---- mbarrier ---------------------------------------------------------------
+// A barrier's memory may be initialised again only after mbarrier.inval (and
+// with no arrival or transaction still pending on it).
+__device__ __forceinline__ void mbar_inval(uint64_t* m) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(m)) : "memory");
+}
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(m)), "r"(count) : "memory");
 }

@@ -170,3 +170,23 @@ def test_async_step_matches_sync(lib, prec, method):
     (W1, H1, l1), (W2, H2, l2) = outs
     assert np.array_equal(W1, W2) and np.array_equal(H1, H2)
     assert l1 == l2
+
+
+@pytest.mark.parametrize("order,beta,K,F,N", [("W", 2.0, 49, 300, 4100), ("H", 0.0, 20, 300, 4100),
+                                               ("H", 1.0, 8, 200, 20000), ("W", 1.5, 64, 300, 4100)])
+def test_tf32_persistent_step_kernel(lib, monkeypatch, order, beta, K, F, N):
+    """NMF_TC_STEP=1: the whole JMM iteration in one cooperative launch (grid
+    barriers between the phases, several units per block when the sweeps have
+    more units than SMs) gives the oracle's iterates and objective, and
+    agrees with the per-kernel sequence."""
+    monkeypatch.setenv("NMF_TC_STEP", "1")
+    V, W0, H0 = problem(F, N, K, seed=21)         # N = 20000: more column-sweep units than SMs
+    W, H, loss, _ = run_tc(V, W0, H0, beta, "jmm", 3, order)
+    Wo, Ho, lo = O.run(V, W0, H0, beta, iters=3, order=order)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[2], rel=TF32_LOSS_RTOL)
+    monkeypatch.delenv("NMF_TC_STEP")
+    W1, H1, loss1, _ = run_tc(V, W0, H0, beta, "jmm", 3, order)
+    assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
+    assert loss == pytest.approx(loss1, rel=1e-4)
