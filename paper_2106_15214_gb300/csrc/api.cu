@@ -226,14 +226,32 @@ void tc_tiling(Prob<float>& P, int sms) {
   tc_split(P.tcRowTiles, P.N, kp, sms, P.tcChunkN, P.tcSplitS, P.tcClusterS, P.tcS);
   P.tcColTiles = (int)cdiv(P.N, 128);
   tc_split(P.tcColTiles, P.F, kp, sms, P.tcChunkF, P.tcSplitR, P.tcClusterR, P.tcR);
+  // Column sweep over more than one wave of blocks (e.g. 157 column tiles on
+  // 152 SMs): split its tile steps stream-K over one wave instead
+  // (warp-specialised kernel only; NMF_TC_SK=0 keeps the uniform split).
+  P.tcSK = 0;
+  P.tcSKBlocks = 0;
+  const char* skEnv = std::getenv("NMF_TC_SK");
+  const bool skOn = !(skEnv && skEnv[0] == '0');
+  const int64_t units = (int64_t)P.tcColTiles * P.tcSplitR;
+  if (skOn && kp <= 64 && P.tcClusterR == 1 && units > sms) {
+    const int64_t ft = cdiv(P.F, 32), T = (int64_t)P.tcColTiles * ft;
+    const int64_t G = std::min<int64_t>(sms, T);
+    int most = 1;
+    for (int64_t nt = 0; nt < P.tcColTiles; ++nt) most = std::max(most, sk_slices(nt, ft, T, G));
+    P.tcSK = 1;
+    P.tcSKBlocks = (int)G;
+    P.tcR = most;
+  }
   if (std::getenv("NMF_TC_DEBUG"))
     std::fprintf(stderr, "nmf tc capacity (blocks resident) cluster 1/2/4/8: %d %d %d %d (sms %d)\n",
                  tc_ws_capacity(kp, 1), tc_ws_capacity(kp, 2), tc_ws_capacity(kp, 4), tc_ws_capacity(kp, 8), sms);
   if (std::getenv("NMF_TC_DEBUG"))
     std::fprintf(stderr, "nmf tc tiling F=%lld N=%lld K=%d: row %d tiles x %d blocks (cluster %d, %d slices, chunk %lld); "
-                 "col %d tiles x %d blocks (cluster %d, %d slices, chunk %lld)\n",
+                 "col %d tiles x %d blocks (cluster %d, %d slices, chunk %lld, stream-K %d blocks)\n",
                  (long long)P.F, (long long)P.N, P.K, P.tcRowTiles, P.tcSplitS, P.tcClusterS, P.tcS,
-                 (long long)P.tcChunkN, P.tcColTiles, P.tcSplitR, P.tcClusterR, P.tcR, (long long)P.tcChunkF);
+                 (long long)P.tcChunkN, P.tcColTiles, P.tcSplitR, P.tcClusterR, P.tcR, (long long)P.tcChunkF,
+                 P.tcSK ? P.tcSKBlocks : 0);
 }
 template <typename T> void tc_tiling(Prob<T>&, int) {}
 
@@ -258,6 +276,7 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     probs[i].tcS = probs[i].tcR = 1;
     probs[i].tcSplitS = probs[i].tcSplitR = 1;
     probs[i].tcClusterS = probs[i].tcClusterR = 1;
+    probs[i].tcSK = probs[i].tcSKBlocks = 0;
     if (!c->batched) tc_tiling(probs[i], c->sms);
     const int Smax = std::max(tl[i].S, probs[i].tcS), Rmax = std::max(tl[i].R, probs[i].tcR);
     const size_t FK = (size_t)F * K, KN = (size_t)K * N;
@@ -335,7 +354,8 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   all.insert(all.end(), pw.begin(), pw.end());
   all.insert(all.end(), ph.begin(), ph.end());
   all.insert(all.end(), pk.begin(), pk.end());
-  const int tcRowGrid = probs[0].tcRowTiles * probs[0].tcSplitS, tcColGrid = probs[0].tcColTiles * probs[0].tcSplitR;
+  const int tcRowGrid = probs[0].tcRowTiles * probs[0].tcSplitS;
+  const int tcColGrid = probs[0].tcSK ? probs[0].tcSKBlocks : probs[0].tcColTiles * probs[0].tcSplitR;
   all.insert(all.end(), {0, c->batched ? 0 : tcRowGrid, 0, c->batched ? 0 : tcColGrid});
   NMF_CU(cudaMemcpy(tabs, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
   pl.d_prefTc = tabs + 5 * (cnt + 1);
@@ -512,7 +532,8 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   // into the epilogues (EpiFuse); batched contexts use the separate kernels
   const bool fuse = !c->batched;
   const int rowGrid = tc ? c->hpf[0].tcRowTiles * c->hpf[0].tcSplitS : pl.totRow;
-  const int colGrid = tc ? c->hpf[0].tcColTiles * c->hpf[0].tcSplitR : pl.totCol;
+  const int colGrid = tc ? (c->hpf[0].tcSK ? c->hpf[0].tcSKBlocks : c->hpf[0].tcColTiles * c->hpf[0].tcSplitR)
+                       : pl.totCol;
   auto fz_for = [&](int flags, bool lossFromRow) {
     EpiFuse f;
     if (!fuse) return f;

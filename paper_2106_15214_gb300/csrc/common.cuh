@@ -82,6 +82,8 @@ struct Prob {
   int tcClusterS;    // blocks of one cluster, combined through distributed shared memory
   int tcSplitR;      // blocks along F per column tile (padded to a multiple of tcClusterR)
   int tcClusterR;
+  int tcSK;          // 1: the column sweep is split stream-K (below), tcR = most slices of any column tile
+  int tcSKBlocks;    // blocks of the stream-K column sweep
   int64_t tcChunkN;  // multiple of 32
   int64_t tcChunkF;  // multiple of 32
   // TF32-rounded, zero-padded operand copies read by TMA in the tensor-core
@@ -98,6 +100,17 @@ struct Prob {
   int kp, ks;
   int64_t Fp, Np;
 };
+
+// Stream-K split of the tensor-core column sweep: its T = tiles x ft tile
+// steps (ft = ceil(F / 32) per column tile, tile-major) are cut into G equal
+// contiguous ranges, block g taking [floor(g T / G), floor((g + 1) T / G)).
+// A column tile is then covered by a few consecutive blocks; block g writes
+// its part of tile nt into slice g - first block of nt.
+__host__ __device__ inline int64_t sk_block_of(int64_t step, int64_t T, int64_t G) { return ((step + 1) * G - 1) / T; }
+__host__ __device__ inline int sk_slices(int64_t nt, int64_t ft, int64_t T, int64_t G) {
+  return (int)(sk_block_of((nt + 1) * ft - 1, T, G) - sk_block_of(nt * ft, T, G) + 1);
+}
+
 
 // Finds the problem owning linear block index `b` given an exclusive prefix
 // table of block counts (prefix[count] = total).

@@ -451,7 +451,12 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
   const int64_t idx = (int64_t)(b - prefix[pi]) * EW + threadIdx.x;
   if (idx < KN && !skip) {
     T num, den;
-    sum_slices(P.colPart + idx, 2 * KN, KN, tc ? P.tcR : P.R, num, den);
+    int slices = tc ? P.tcR : P.R;
+    if (tc && P.tcSK) {                                  // stream-K: this column tile's own count
+      const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft;
+      slices = sk_slices((idx % P.N) / 128, ft, T, P.tcSKBlocks);
+    }
+    sum_slices(P.colPart + idx, 2 * KN, KN, slices, num, den);
     if (mode == EPI_GRAD) {
       gout[idx] = den - num;
     } else {

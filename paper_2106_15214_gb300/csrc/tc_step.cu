@@ -296,13 +296,19 @@ tc_step_kernel(const __grid_constant__ StepMaps M, Prob<float> P, BetaParams bp,
   {
     const bool skip = status_set(S.status);
     if (S.wfirst) {
-      for (int u = blockIdx.x; u < S.rowUnits; u += S.G)
-        ws_unit<BK, false, true>(M.rV, M.rOnce, M.rFa, M.rD1, M.rD2, S.useTmaR, S.nopR, S.nvR, P, lossFlag, bp,
-                                 S.lossPart, S.status, u, skip, base, tbase, bars, s_abort, red, nullptr, true);
+      for (int u = blockIdx.x; u < S.rowUnits; u += S.G) {
+        const double l = ws_unit<BK, false, true>(M.rV, M.rOnce, M.rFa, M.rD1, M.rD2, S.useTmaR, S.nopR, S.nvR, P,
+                                                  lossFlag, bp, S.status, uniform_geom<true>(P, u), skip, base, tbase,
+                                                  bars, s_abort, red, nullptr, true);
+        if (lossFlag && threadIdx.x == 0) S.lossPart[u] = l;
+      }
     } else {
-      for (int u = blockIdx.x; u < S.colUnits; u += S.G)
-        ws_unit<BK, false, false>(M.cV, M.cOnce, M.cFa, M.cD1, M.cD2, S.useTmaC, S.nopC, S.nvC, P, lossFlag, bp,
-                                  S.lossPart, S.status, u, skip, base, tbase, bars, s_abort, red, nullptr, true);
+      for (int u = blockIdx.x; u < S.colUnits; u += S.G) {
+        const double l = ws_unit<BK, false, false>(M.cV, M.cOnce, M.cFa, M.cD1, M.cD2, S.useTmaC, S.nopC, S.nvC, P,
+                                                   lossFlag, bp, S.status, uniform_geom<false>(P, u), skip, base,
+                                                   tbase, bars, s_abort, red, nullptr, true);
+        if (lossFlag && threadIdx.x == 0) S.lossPart[u] = l;
+      }
     }
   }
   grid_sync(S);
@@ -334,11 +340,11 @@ tc_step_kernel(const __grid_constant__ StepMaps M, Prob<float> P, BetaParams bp,
     }
     for (int u = blockIdx.x; u < units; u += S.G) {
       if (S.wfirst)
-        ws_unit<BK, true, false>(M.cV, M.cOnce, M.cFa, M.cD1, M.cD2, S.useTmaC, S.nopC, S.nvC, P, 0, bp,
-                                 S.lossPart, S.status, u, skip, base, tbase, bars, s_abort, red, sp, true);
+        ws_unit<BK, true, false>(M.cV, M.cOnce, M.cFa, M.cD1, M.cD2, S.useTmaC, S.nopC, S.nvC, P, 0, bp, S.status,
+                                 uniform_geom<false>(P, u), skip, base, tbase, bars, s_abort, red, sp, true);
       else
-        ws_unit<BK, true, true>(M.rV, M.rOnce, M.rFa, M.rD1, M.rD2, S.useTmaR, S.nopR, S.nvR, P, 0, bp,
-                                S.lossPart, S.status, u, skip, base, tbase, bars, s_abort, red, sp, true);
+        ws_unit<BK, true, true>(M.rV, M.rOnce, M.rFa, M.rD1, M.rD2, S.useTmaR, S.nopR, S.nvR, P, 0, bp, S.status,
+                                uniform_geom<true>(P, u), skip, base, tbase, bars, s_abort, red, sp, true);
       sp = nullptr;                                  // the side job runs with the block's first unit only
     }
   }
@@ -372,7 +378,7 @@ size_t step_smem(int kp, int* nopR, int* nvR, int* nopC, int* nvC, bool wfirst) 
 }  // namespace
 
 bool tc_step_supported(const Prob<float>& P, const TcMaps& m, int sms) {
-  if (!m.ok || !P.sWS || P.kp > 64 || P.tcClusterS != 1 || P.tcClusterR != 1) return false;
+  if (!m.ok || !P.sWS || P.kp > 64 || P.tcClusterS != 1 || P.tcClusterR != 1 || P.tcSK) return false;
   if (P.K > WS_THREADS / 8) return false;            // norm reductions assume >= 8 threads per column
   (void)sms;
   return true;

@@ -449,7 +449,7 @@ cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int ws
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
   if (kp <= 64 && maps && maps->ok) return launch_tc_ws_col(P, *maps, csel, flags, bp, lossPart, status, st);
-  if (P.tcClusterR != 1) return cudaErrorNotSupported;
+  if (P.tcClusterR != 1 || P.tcSK) return cudaErrorNotSupported;   // clustered / stream-K splits need the warp-specialised kernel
   const size_t sm = col_smem(kp);
   const unsigned grid = (unsigned)(P.tcColTiles * P.tcSplitR);
   NMF_TC_BK_DISPATCH(tc_col_sweep_kernel, grid, sm, P, wsel, hsel, csel, flags, bp, lossPart, status);

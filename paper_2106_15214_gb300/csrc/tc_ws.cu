@@ -76,7 +76,8 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   if (csize > 1 && lay.total - lay.fa0 < 2048u * kp) return cudaErrorInvalidValue;
   // the row sweep stages its [P | Q] tile (2 x 128 x (K | 1) floats) over the stage ring and the A/B tiles
   if (ROW && lay.total - lay.fa0 < 2u * MT * (uint32_t)(P.K | 1) * 4u) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcSplitS : P.tcColTiles * P.tcSplitR);
+  const bool sk = !ROW && P.tcSK;
+  const unsigned grid = (unsigned)(ROW ? P.tcRowTiles * P.tcSplitS : (sk ? P.tcSKBlocks : P.tcColTiles * P.tcSplitR));
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(grid);
@@ -95,10 +96,17 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
   cudaError_t e = cudaSuccess;
 #define NMF_WS_CASE(BKV)                                                                                   \
   case BKV:                                                                                                \
-    e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                              \
-    if (e == cudaSuccess)                                                                                  \
-      e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, bp, \
-                             lossPart, status);                                                            \
+    if (sk) {                                                                                              \
+      e = prep(tc_ws_sk_kernel<BKV, CHI>, sm);                                                              \
+      if (e == cudaSuccess)                                                                                \
+        e = cudaLaunchKernelEx(&cfg, tc_ws_sk_kernel<BKV, CHI>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, \
+                               bp, lossPart, status);                                                      \
+    } else {                                                                                               \
+      e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                            \
+      if (e == cudaSuccess)                                                                                \
+        e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, \
+                               bp, lossPart, status);                                                      \
+    }                                                                                                      \
     break;
   switch (bp.kind) {
     NMF_WS_CASE(BK_IS)

@@ -163,28 +163,50 @@ __device__ __forceinline__ void side_run(const SideJob* side, int lane) {
   }
 }
 
+// What one unit covers: the 128-wide tile mt of the fixed dimension, the
+// streamed range [s0, s1), the partial slice it writes (outSlice; with a
+// cluster, the blocks of slices sl .. sl + c - 1 write slice sl / c).
+struct UnitGeom {
+  int mt, sl, outSlice;
+  int64_t s0, s1;
+};
+
+// The uniform split: unit = mt * split + sl, chunks of tcChunkN / tcChunkF.
+template <bool ROW>
+__device__ __forceinline__ UnitGeom uniform_geom(const Prob<float>& P, int unit) {
+  UnitGeom g;
+  const int split = ROW ? P.tcSplitS : P.tcSplitR;
+  const int csize = ROW ? P.tcClusterS : P.tcClusterR;
+  g.mt = unit / split;
+  g.sl = unit % split;
+  g.outSlice = g.sl / csize;
+  const int64_t chunk = ROW ? P.tcChunkN : P.tcChunkF;
+  const int64_t sLim = ROW ? P.N : P.F;
+  g.s0 = (int64_t)g.sl * chunk;
+  g.s1 = g.s0 + chunk < sLim ? g.s0 + chunk : sLim;
+  return g;
+}
+
+// Returns the unit's objective partial (valid in thread 0; 0 without SWEEP_LOSS).
 template <int BK, bool CHI, bool ROW>
-__device__ __forceinline__ void ws_unit(const CUtensorMap& tmV, const CUtensorMap& tmOnce, const CUtensorMap& tmFa,
-                                        const CUtensorMap& tmD1, const CUtensorMap& tmD2, int useTma, int nop,
-                                        int nv, const Prob<float>& P, int flags, const BetaParams& bp,
-                                        double* __restrict__ lossPart, int* __restrict__ status, int unit,
-                                        bool skip, unsigned char* base, uint32_t tbase, Bars& bars,
-                                        volatile int& s_abort, double* red, const SideJob* side,
-                                        bool reuse) {
+__device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensorMap& tmOnce, const CUtensorMap& tmFa,
+                                          const CUtensorMap& tmD1, const CUtensorMap& tmD2, int useTma, int nop,
+                                          int nv, const Prob<float>& P, int flags, const BetaParams& bp,
+                                          int* __restrict__ status, const UnitGeom& geo, bool skip,
+                                          unsigned char* base, uint32_t tbase, Bars& bars, volatile int& s_abort,
+                                          double* red, const SideJob* side, bool reuse) {
   const int K = P.K, kp = (K + 15) & ~15, na = (kp + 31) / 32;
   const WsLayout L = ws_layout(kp, CHI, nop, nv);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // block coordinates: the fixed 128-wide dimension (m0) and the streamed chunk [s0, s1)
+  // the fixed 128-wide dimension (m0) and the streamed range [s0, s1)
   // (blocks of one tile are consecutive, so a cluster shares m0)
-  const int split = ROW ? P.tcSplitS : P.tcSplitR;
   const int csize = ROW ? P.tcClusterS : P.tcClusterR;
-  const int mt = unit / split, sl = unit % split;
+  const int mt = geo.mt, sl = geo.sl;
   const int64_t m0 = (int64_t)mt * MT;
   const int64_t mLim = ROW ? P.F : P.N;
-  const int64_t chunk = ROW ? P.tcChunkN : P.tcChunkF;
   const int64_t sLim = ROW ? P.N : P.F;
-  const int64_t s0 = (int64_t)sl * chunk;
-  const int64_t s1 = s0 + chunk < sLim ? s0 + chunk : sLim;
+  const int64_t s0 = geo.s0;
+  const int64_t s1 = geo.s1;
   // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
   const int ntilesGeom = s0 < sLim ? (int)((s1 - s0 + TL - 1) / TL) : 0;
   const bool wantLoss = flags & SWEEP_LOSS;
@@ -575,7 +597,7 @@ __device__ __forceinline__ void ws_unit(const CUtensorMap& tmV, const CUtensorMa
     if (sl % csize == 0) {
       const int nrows = (int)(mLim - m0 < MT ? mLim - m0 : MT);
       const int cnt = nrows * K;
-      float* outP = P.rowPart + (int64_t)(sl / csize) * 2 * P.F * K + m0 * K;
+      float* outP = P.rowPart + (int64_t)geo.outSlice * 2 * P.F * K + m0 * K;
       float* outQ = outP + P.F * K;
       for (int i = tid; i < cnt; i += WS_THREADS) {
         const int r = i / K, c = i - r * K;
@@ -587,16 +609,14 @@ __device__ __forceinline__ void ws_unit(const CUtensorMap& tmV, const CUtensorMa
     const int64_t gm = m0 + mrow;
     if (gm < mLim) {
       const int64_t KN = (int64_t)K * P.N;
-      float* part = P.colPart + (int64_t)(sl / csize) * 2 * KN + (isQ ? KN : 0) + (int64_t)col0 * P.N + gm;
+      float* part = P.colPart + (int64_t)geo.outSlice * 2 * KN + (isQ ? KN : 0) + (int64_t)col0 * P.N + gm;
       #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j < per && col0 + j < K) part[(int64_t)j * P.N] = acc[j];
     }
   }
-  if (wantLoss) {
-    const double tt = block_sum(loss, red);
-    if (tid == 0) lossPart[unit] = tt;
-  }
+  double unitLoss = 0.0;
+  if (wantLoss) unitLoss = block_sum(loss, red);
   fence_before_sync();
   __syncthreads();
   if (s_abort) mbar_wait(&bars.done, 0u, 100000000ull);
@@ -629,6 +649,7 @@ __device__ __forceinline__ void ws_unit(const CUtensorMap& tmV, const CUtensorMa
     mbar_inval(&bars.done);
   }
   if (reuse) __syncthreads();
+  return unitLoss;
 }
 
 // One launch, one unit per block.
@@ -653,8 +674,52 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   // writes (the factor copies, the status word) are visible
   pdl_wait();
   const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
-  ws_unit<BK, CHI, ROW>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, lossPart, status, blockIdx.x,
-                        skip, base, tslot, bars, s_abort, red, nullptr, false);
+  const double l = ws_unit<BK, CHI, ROW>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status,
+                                         uniform_geom<ROW>(P, blockIdx.x), skip, base, tslot, bars, s_abort, red,
+                                         nullptr, false);
+  if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
+  if ((threadIdx.x >> 5) == 2) tmem_dealloc(tslot, TM_COLS);
+}
+
+// Stream-K column sweep: block g runs its range of tile steps as one unit per
+// column tile it touches (see sk_block_of); the objective partial of the
+// block is the sum of its units'.
+template <int BK, bool CHI>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmOnce,
+                const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
+                const __grid_constant__ CUtensorMap tmD2, int useTma, int nop, int nv, Prob<float> P, int flags,
+                BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
+  pdl_trigger();
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ Bars bars;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int s_abort;
+  __shared__ double red[32];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  if ((threadIdx.x >> 5) == 2) tmem_alloc(&tslot, TM_COLS);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  pdl_wait();
+  const bool skip = *status != 0;
+  const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft, G = gridDim.x;
+  const int64_t a = (int64_t)blockIdx.x * T / G, b = ((int64_t)blockIdx.x + 1) * T / G;
+  double l = 0.0;
+  for (int64_t st = a; st < b;) {
+    const int64_t nt = st / ft;
+    const int64_t e = (nt + 1) * ft < b ? (nt + 1) * ft : b;
+    UnitGeom geo;
+    geo.mt = (int)nt;
+    geo.sl = 0;
+    geo.outSlice = (int)(blockIdx.x - sk_block_of(nt * ft, T, G));
+    geo.s0 = (st - nt * ft) * TL;
+    geo.s1 = (e - nt * ft) * TL < P.F ? (e - nt * ft) * TL : P.F;
+    l += ws_unit<BK, CHI, false>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status, geo, skip, base,
+                                 tslot, bars, s_abort, red, nullptr, e < b);
+    st = e;
+  }
+  if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
   if ((threadIdx.x >> 5) == 2) tmem_dealloc(tslot, TM_COLS);
 }
 

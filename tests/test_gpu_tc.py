@@ -190,3 +190,20 @@ def test_tf32_persistent_step_kernel(lib, monkeypatch, order, beta, K, F, N):
     W1, H1, loss1, _ = run_tc(V, W0, H0, beta, "jmm", 3, order)
     assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
     assert loss == pytest.approx(loss1, rel=1e-4)
+
+
+@pytest.mark.parametrize("order,method,K", [("H", "jmm", 20), ("W", "jmm", 33), ("H", "bmm", 16)])
+def test_tf32_stream_k_column_sweep(lib, monkeypatch, order, method, K):
+    """157 column tiles on 152 SMs: the column sweep is split stream-K (block
+    ranges cross column tiles, per-tile slice counts in the H epilogue) and
+    matches the oracle and the uniform split (NMF_TC_SK=0)."""
+    V, W0, H0 = problem(300, 20000, K, seed=23)
+    W, H, loss, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
+    Wo, Ho, lo = O.run(V, W0, H0, 1.0, method=method, iters=2, order=order)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[1], rel=TF32_LOSS_RTOL)
+    monkeypatch.setenv("NMF_TC_SK", "0")
+    W1, H1, loss1, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
+    assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
+    assert loss == pytest.approx(loss1, rel=1e-4)
