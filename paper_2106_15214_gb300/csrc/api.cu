@@ -413,6 +413,9 @@ nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     }
     oW += (size_t)P.F * P.K; oH += (size_t)P.K * P.N; oV += (size_t)P.F * P.N;
   }
+  // 16-byte H epilogue: one float problem, N % 4 == 0 and the caller's H aligned
+  pl.colVec4 = (!c->batched && c->count == 1 && sizeof(T) == 4 && c->N[0] % 4 == 0 &&
+                (reinterpret_cast<uintptr_t>(c->H) & 15u) == 0) ? 1 : 0;
   NMF_CU(cudaMemcpyAsync(pl.d_probs, probs.data(), sizeof(Prob<T>) * c->count,
                          cudaMemcpyHostToDevice, c->stream));
   c->tableDirty = false;
@@ -495,7 +498,10 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
                       (c->order == NMF_ORDER_AUTO && c->F[0] >= c->N[0]);
   const int L = c->L;
   const int C = SWEEP_CONTRACT;
-  const int tci = tc ? 1 : 0;
+  // 2: tensor-core path whose sweeps read only the TF32 copies of chi
+  // (warp-specialised kernels), so the epilogues skip the full-precision chi
+  int tci = tc ? 1 : 0;
+  if (tc && c->tcmaps.ok && c->count == 1 && c->hpf[0].kp <= 64) tci = 2;
   auto row_sweep = [&](int wsel, int hsel, int dsel, int flags) -> nmf_status {
     if constexpr (std::is_same<T, float>::value) {
       if (tc)

@@ -133,6 +133,7 @@ struct Plan {
   int* d_prefK = nullptr; int totK = 0;       // one block per column of W
   int* d_prefTc = nullptr;                    // {0, tc row grid, 0, tc column grid} (single problem)
   int rowSlices[2] = {1, 1};                  // row-sweep partial slices: SIMT, tensor core (single problem)
+  int colVec4 = 0;                            // single problem with N % 4 == 0: 16-byte H epilogue
 };
 
 template <typename T>

@@ -396,8 +396,10 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
       if (want_chi) {
         T c1, c2;
         chi_terms<BK, T>(x, P.Wt[idx], (T)bp.beta, c1, c2);
-        P.chiW1[idx] = c1;
-        P.chiW2[idx] = c2;
+        if (tc != 2) {                            // tc == 2: the sweeps read only the TF32 copies below
+          P.chiW1[idx] = c1;
+          P.chiW2[idx] = c2;
+        }
         if (tc && P.sCW1) {                       // transposed TF32 copies for the tensor-core sweeps
           const int64_t f = idx / P.K, k = idx - f * P.K;
           P.sCW1[k * P.Fp + f] = tf32_round(c1);
@@ -466,8 +468,10 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
       if (want_chi) {
         T c1, c2;
         chi_terms<BK, T>(x, P.Ht[idx], (T)bp.beta, c1, c2);
-        P.chiH1[idx] = c1;
-        P.chiH2[idx] = c2;
+        if (tc != 2) {
+          P.chiH1[idx] = c1;
+          P.chiH2[idx] = c2;
+        }
         if (tc && P.sCH1) {
           const int64_t k = idx / P.N, n = idx - k * P.N;
           P.sCH1[k * P.Np + n] = tf32_round(c1);
@@ -483,6 +487,89 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     }
   }
   if (fz.flags & FUSE_LOSS) last_block_finalize<T>(fz, P, totH, nullptr);
+}
+
+// The H epilogue above (MU update only) for one float problem with N % 4 == 0
+// and H 16-byte aligned: each thread takes four consecutive columns of one
+// row of H (same column tile, same norm), with 16-byte loads and stores; the
+// arithmetic is the same per entry. Blocks [totQ, ...) divide W's columns by
+// the norms as above.
+template <int BK>
+__global__ void __launch_bounds__(EW)
+cols_epilogue_vec4_kernel(const Prob<float>* __restrict__ probs, int basesel, int want_chi, BetaParams bp,
+                          int* __restrict__ status, int tc, EpiFuse fz, int totQ) {
+  pdl_trigger();
+  pdl_wait();
+  const bool skip = *status != 0;
+  if (skip && !(fz.flags & FUSE_LOSS)) return;
+  const int b = blockIdx.x;
+  const Prob<float> P = probs[0];
+  if ((fz.flags & FUSE_NORM_APPLY) && b >= totQ) {      // W /= norms
+    const int64_t idx = (int64_t)(b - totQ) * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const float nk = P.norms[idx % P.K];
+      if (nk > 0.f) P.W[idx] = P.W[idx] / nk;
+    }
+    return;
+  }
+  const int64_t KN = (int64_t)P.K * P.N;
+  const int64_t idx = 4 * ((int64_t)b * EW + threadIdx.x);
+  if (idx < KN && !skip) {
+    const int64_t k = idx / P.N, n = idx - k * P.N;
+    int slices = tc ? P.tcR : P.R;
+    if (tc && P.tcSK) {
+      const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft;
+      slices = sk_slices(n / 128, ft, T, P.tcSKBlocks);
+    }
+    float4 num = make_float4(0.f, 0.f, 0.f, 0.f), den = num;
+    const float* part = P.colPart + idx;
+    for (int s0 = 0; s0 < slices; s0 += 4) {           // four slices' loads in flight, added in slice order
+      float4 vn[4], vd[4];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int sl = s0 + u;
+        vn[u] = sl < slices ? *reinterpret_cast<const float4*>(part + (int64_t)sl * 2 * KN) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vd[u] = sl < slices ? *reinterpret_cast<const float4*>(part + (int64_t)sl * 2 * KN + KN)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        num.x += vn[u].x; num.y += vn[u].y; num.z += vn[u].z; num.w += vn[u].w;
+        den.x += vd[u].x; den.y += vd[u].y; den.z += vd[u].z; den.w += vd[u].w;
+      }
+    }
+    const float nv[4] = {num.x, num.y, num.z, num.w}, dv[4] = {den.x, den.y, den.z, den.w};
+    {
+      const float4 ht4 = *reinterpret_cast<const float4*>(P.Ht + idx);
+      const float4 b4 = basesel == SEL_TILDE ? ht4 : *reinterpret_cast<const float4*>(P.H + idx);
+      const float ht[4] = {ht4.x, ht4.y, ht4.z, ht4.w}, bs[4] = {b4.x, b4.y, b4.z, b4.w};
+      const float nk = (fz.flags & FUSE_NORM_APPLY) ? P.norms[k] : 0.f;
+      float y[4], c1[4], c2[4];
+      bool finite = true;
+      #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float x = bs[j] * mu_ratio<BK, float>(nv[j], dv[j], (float)bp.gamma);
+        finite = finite && isfinite(x);
+        if (want_chi) chi_terms<BK, float>(x, ht[j], (float)bp.beta, c1[j], c2[j]);
+        y[j] = ((fz.flags & FUSE_NORM_APPLY) && nk > 0.f) ? x * nk : x;
+      }
+      if (!finite) atomicExch(status, 4);
+      if (want_chi) {
+        if (tc != 2) {
+          *reinterpret_cast<float4*>(P.chiH1 + idx) = make_float4(c1[0], c1[1], c1[2], c1[3]);
+          *reinterpret_cast<float4*>(P.chiH2 + idx) = make_float4(c2[0], c2[1], c2[2], c2[3]);
+        }
+        if (tc && P.sCH1) {
+          *reinterpret_cast<float4*>(P.sCH1 + k * P.Np + n) =
+              make_float4(tf32_round(c1[0]), tf32_round(c1[1]), tf32_round(c1[2]), tf32_round(c1[3]));
+          *reinterpret_cast<float4*>(P.sCH2 + k * P.Np + n) =
+              make_float4(tf32_round(c2[0]), tf32_round(c2[1]), tf32_round(c2[2]), tf32_round(c2[3]));
+        }
+      }
+      *reinterpret_cast<float4*>(P.H + idx) = make_float4(y[0], y[1], y[2], y[3]);
+    }
+  }
+  if (fz.flags & FUSE_LOSS) last_block_finalize<float>(fz, P, totQ, nullptr);
 }
 
 // Blocks [0, totW) copy W -> Wt, blocks [totW, totW + totH) copy H -> Ht.
@@ -782,6 +869,16 @@ cudaError_t rows_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
 template <typename T, int BK>
 cudaError_t cols_epi_bk(const Plan<T>& pl, int mode, int basesel, int want_chi,
                         const BetaParams& bp, T* gout, int* status, cudaStream_t st, int tc, const EpiFuse& fz) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (pl.colVec4 && mode != EPI_GRAD) {                // (gradient buffers are the caller's: alignment unknown)
+      const int totQ = (pl.totH + 3) / 4;               // totH blocks of EW entries -> quads
+      const int grid = totQ + ((fz.flags & FUSE_NORM_APPLY) ? pl.totW : 0);
+      const cudaError_t le_ = launch_pdl(cols_epilogue_vec4_kernel<BK>, dim3(grid), dim3(EW), 0, st,
+                                         (const Prob<float>*)pl.d_probs, basesel, want_chi, bp, status, tc, fz, totQ);
+      if (le_ != cudaSuccess) return le_;
+      return cudaGetLastError();
+    }
+  }
   const int grid = pl.totH + ((fz.flags & FUSE_NORM_APPLY) ? pl.totW : 0);
   {
     const cudaError_t le_ = launch_pdl(cols_epilogue_kernel<T, BK>, dim3(grid), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefH, mode, basesel, want_chi, bp, gout, status, tc, fz, pl.totH);
