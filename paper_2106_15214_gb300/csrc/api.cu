@@ -502,22 +502,24 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   // (warp-specialised kernels), so the epilogues skip the full-precision chi
   int tci = tc ? 1 : 0;
   if (tc && c->tcmaps.ok && c->count == 1 && c->hpf[0].kp <= 64) tci = 2;
-  auto row_sweep = [&](int wsel, int hsel, int dsel, int flags) -> nmf_status {
+  auto row_sweep = [&](int wsel, int hsel, int dsel, int flags, const SideJob* side = nullptr) -> nmf_status {
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
         return cu(timed(&c->timer, st, "tc_row_sweep", 1, [&] {
-          return launch_tc_row_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, dsel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+          return launch_tc_row_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, dsel, flags, c->prec == NMF_BF16, bp, lp,
+                                     status, st, side);
         }));
     }
     return cu(timed(&c->timer, st, "row_sweep", 1, [&] {
       return launch_row_sweep<T>(pl, wsel, hsel, dsel, flags, bp, lp, status, st);
     }));
   };
-  auto col_sweep = [&](int wsel, int hsel, int csel, int flags) -> nmf_status {
+  auto col_sweep = [&](int wsel, int hsel, int csel, int flags, const SideJob* side = nullptr) -> nmf_status {
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
         return cu(timed(&c->timer, st, "tc_col_sweep", 1, [&] {
-          return launch_tc_col_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, csel, flags, c->prec == NMF_BF16, bp, lp, status, st);
+          return launch_tc_col_sweep(c->hpf[0], &c->tcmaps, wsel, hsel, csel, flags, c->prec == NMF_BF16, bp, lp,
+                                     status, st, side);
         }));
     }
     return cu(timed(&c->timer, st, "col_sweep", 1, [&] {
@@ -604,6 +606,37 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
       NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
     }
     bool normDone = false;
+    // Warp-specialised path, L = 1: the W epilogue only writes the norm
+    // partials; the next sweep's idle warps reduce them (and the objective of
+    // the first sweep), or (H first) the normalisation kernel does.
+    const bool sideScheme = tci == 2 && joint && L == 1 && fuse && norm;
+    if (sideScheme) {
+      SideJob sj;
+      const int nparts = rows_epilogue_grid(pl.totW, rows_epilogue_lanes(pl, tci));
+      if (lossHere) {
+        sj.lossPart = lp;
+        sj.nloss = wfirst ? rowGrid : colGrid;
+        sj.lossOut = c->d_lossOut;
+      }
+      if (wfirst) {
+        sj.normPart = reinterpret_cast<const float*>(c->d_normPart);
+        sj.nparts = nparts;
+        if constexpr (std::is_same<T, float>::value) sj.norms = c->hpf[0].norms;
+        NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
+        NMF_TRY(rows_epi(SEL_TILDE, 1, FUSE_NORM_PART | FUSE_NO_FINALIZE));
+        NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C, &sj));
+        NMF_TRY(cols_epi(SEL_TILDE, 0, FUSE_NORM_APPLY));
+      } else {
+        NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
+        NMF_TRY(cols_epi(SEL_TILDE, 1, 0));
+        NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C, lossHere ? &sj : nullptr));
+        NMF_TRY(rows_epi(SEL_TILDE, 0, FUSE_NORM_PART | FUSE_NO_FINALIZE));
+        NMF_CU(timed(&c->timer, st, "normalize", 1, [&] {
+          return launch_normalize_parts<T>(pl, reinterpret_cast<const T*>(c->d_normPart), nparts, status, st);
+        }));
+      }
+      continue;
+    }
     if (joint) {
       for (int l = 1; l <= L; ++l) {
         const int f1 = l == 1 ? CL : C;

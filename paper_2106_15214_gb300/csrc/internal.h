@@ -151,7 +151,9 @@ cudaError_t launch_col_sweep(const Plan<T>& pl, int wsel, int hsel, int csel, in
 // FUSE_NORM_PART (W epilogue): per-block sums of squares of the new W, turned into
 // the column norms (Prob::norms) by the last block; FUSE_NORM_APPLY (H epilogue):
 // H rows *= norms and W columns /= norms (normalisation, Sec. 4.1.2).
-enum { FUSE_LOSS = 1, FUSE_NORM_PART = 2, FUSE_NORM_APPLY = 4 };
+// FUSE_NO_FINALIZE (with FUSE_NORM_PART): write the partials only; the next
+// tensor-core sweep's idle warps (SideJob) or the normalisation kernel reduce them.
+enum { FUSE_LOSS = 1, FUSE_NORM_PART = 2, FUSE_NORM_APPLY = 4, FUSE_NO_FINALIZE = 8 };
 struct EpiFuse {
   int flags = 0;
   const double* lossPart = nullptr;
@@ -172,6 +174,11 @@ cudaError_t launch_cols_epilogue(const Plan<T>& pl, int mode, int basesel, int w
                                  int tc = 0, const EpiFuse& fz = EpiFuse());
 template <typename T>
 cudaError_t launch_normalize_apply(const Plan<T>& pl, const int* status, cudaStream_t st);
+// Single problem: every block reduces the norm partials ([K][nparts], T)
+// itself (fixed order), then W /= norms, H *= norms.
+template <typename T>
+cudaError_t launch_normalize_parts(const Plan<T>& pl, const T* normPart, int nparts, const int* status,
+                                   cudaStream_t st);
 // Lanes per entry of the W epilogue: for a single problem 8, 4 or 2 with
 // >= 16, >= 8 or >= 4 partial slices, else 1. A single problem runs blocks of
 // 1024 threads (1024 / G entries each), a batched context blocks of EW.
@@ -238,6 +245,23 @@ struct TcMaps {
   bool ok = false;
 };
 bool tc_build_maps(const Prob<float>& P, TcMaps* m);
+
+// Work for the otherwise idle warp 3 of a warp-specialised sweep's blocks:
+// the column norms of W (column k = normK, normK + normStride, ...) from the
+// W epilogue's partials ([k][part], float), and the FP64 objective from the
+// previous sweep's partials (nloss of them). A kernel launch passes the job
+// with normK < 0: block b then takes columns b, b + grid, ..., block 0 the
+// objective.
+struct SideJob {
+  const float* normPart = nullptr;
+  int nparts = 0;
+  int normK = -1;
+  int normStride = 1;
+  float* norms = nullptr;
+  const double* lossPart = nullptr;
+  int nloss = 0;
+  double* lossOut = nullptr;
+};
 // Tensor map of V for the row (row = true) or column sweep; false when V
 // cannot be addressed by TMA (the kernels then load V with cp.async).
 bool tc_map_v(const Prob<float>& P, bool row, CUtensorMap* m);
@@ -263,16 +287,18 @@ cudaError_t launch_tc_step(const Prob<float>& P, const TcMaps& m, const BetaPara
                            int sms, cudaStream_t st);
 
 cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int dsel, int flags,
-                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st,
+                                const SideJob* side = nullptr);
 cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int csel, int flags,
-                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st);
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st,
+                                const SideJob* side = nullptr);
 // Blocks of the warp-specialised sweep (padded rank kp) that can be resident
 // at once when launched in clusters of `csize`; 0 when it cannot launch.
 int tc_ws_capacity(int kp, int csize);
 cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, int flags, const BetaParams& bp,
-                             double* lossPart, int* status, cudaStream_t st);
+                             double* lossPart, int* status, cudaStream_t st, const SideJob* side);
 cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, int flags, const BetaParams& bp,
-                             double* lossPart, int* status, cudaStream_t st);
+                             double* lossPart, int* status, cudaStream_t st, const SideJob* side);
 
 // Sparse beta = 1 path (sparse_kl.cu).
 struct SparseKL {

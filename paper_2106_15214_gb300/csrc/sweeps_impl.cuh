@@ -323,9 +323,16 @@ __device__ __forceinline__ void last_block_finalize(const EpiFuse& fz, const Pro
     }
   }
   if ((fz.flags & FUSE_LOSS) && threadIdx.x < 32) {
-    // the objective in FP64, by one warp: a few partials per lane, one butterfly
+    // the objective in FP64, by one warp: a few partials per lane (loads in
+    // flight together, added in order), one butterfly
     double sl = 0.0;
-    for (int b = threadIdx.x; b < fz.lossBlocks; b += 32) sl += __ldcg(&fz.lossPart[b]);
+    for (int b0 = threadIdx.x; b0 < fz.lossBlocks; b0 += 256) {
+      double v[8];
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = b0 + 32 * u < fz.lossBlocks ? __ldcg(&fz.lossPart[b0 + 32 * u]) : 0.0;
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) sl += v[u];
+    }
     sl = warp_sum(sl);
     if (threadIdx.x == 0) fz.lossOut[0] = sl;
   }
@@ -421,6 +428,7 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
       static_cast<T*>(fz.normPart)[(int64_t)k * gridDim.x + b] = acc;
     }
   }
+  if (fz.flags & FUSE_NO_FINALIZE) return;
   last_block_finalize<T>(fz, P, gridDim.x, s_sq);
 }
 
@@ -570,6 +578,58 @@ cols_epilogue_vec4_kernel(const Prob<float>* __restrict__ probs, int basesel, in
     }
   }
   if (fz.flags & FUSE_LOSS) last_block_finalize<float>(fz, P, totQ, nullptr);
+}
+
+// Normalisation of one problem from the W epilogue's norm partials
+// ([K][nparts]): every block reduces them itself (R threads per column, then
+// a fixed-order sum: the same norms in every block), then blocks [0, totW)
+// divide W's columns by them and blocks [totW, ...) scale H's rows.
+template <typename T>
+__global__ void __launch_bounds__(EW)
+normalize_parts_kernel(const Prob<T>* __restrict__ probs, const T* __restrict__ normPart, int nparts, int totW,
+                       const int* __restrict__ status) {
+  pdl_trigger();
+  pdl_wait();
+  if (*status) return;
+  __shared__ T s_red[EW];
+  __shared__ T s_norm[KMAX];
+  const Prob<T> P = probs[0];
+  const int K = P.K, R = EW / K;
+  T v = T(0);
+  if ((int)threadIdx.x < R * K) {
+    const int k = threadIdx.x / R, j = threadIdx.x - k * R;
+    const T* row = normPart + (int64_t)k * nparts;
+    for (int b0 = j; b0 < nparts; b0 += 4 * R) {
+      T u4[4];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) u4[u] = b0 + u * R < nparts ? row[b0 + u * R] : T(0);
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) v += u4[u];
+    }
+  }
+  s_red[threadIdx.x] = v;
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    T sum = T(0);
+    for (int j = 0; j < R; ++j) sum += s_red[threadIdx.x * R + j];
+    s_norm[threadIdx.x] = sqrt(sum);
+    if (blockIdx.x == 0) P.norms[threadIdx.x] = s_norm[threadIdx.x];
+  }
+  __syncthreads();
+  const int b = blockIdx.x;
+  if (b < totW) {
+    const int64_t idx = (int64_t)b * EW + threadIdx.x;
+    if (idx < P.F * K) {
+      const T nk = s_norm[idx % K];
+      if (nk > T(0)) P.W[idx] = P.W[idx] / nk;
+    }
+  } else {
+    const int64_t idx = (int64_t)(b - totW) * EW + threadIdx.x;
+    if (idx < (int64_t)K * P.N) {
+      const T nk = s_norm[idx / P.N];
+      if (nk > T(0)) P.H[idx] = P.H[idx] * nk;
+    }
+  }
 }
 
 // Blocks [0, totW) copy W -> Wt, blocks [totW, totW + totH) copy H -> Ht.
@@ -911,6 +971,16 @@ cudaError_t launch_normalize_apply(const Plan<T>& pl, const int* status, cudaStr
 }
 
 template <typename T>
+cudaError_t launch_normalize_parts(const Plan<T>& pl, const T* normPart, int nparts, const int* status,
+                                   cudaStream_t st) {
+  if (pl.count != 1 || pl.maxK > EW) return cudaErrorInvalidValue;
+  const cudaError_t le = launch_pdl(normalize_parts_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st,
+                                    (const Prob<T>*)pl.d_probs, normPart, nparts, pl.totW, status);
+  if (le != cudaSuccess) return le;
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st) {
   {
     const cudaError_t le_ = launch_pdl(begin_iteration_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, pl.totW, pl.d_prefH, status);
@@ -955,6 +1025,7 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
                                                T*, int*, cudaStream_t, int, const EpiFuse&);       \
   template cudaError_t launch_normalize_apply<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
+  template cudaError_t launch_normalize_parts<T>(const Plan<T>&, const T*, int, const int*, cudaStream_t); \
   template cudaError_t launch_tc_copies<T>(const Prob<T>&, bool, bool, bool, const int*, cudaStream_t); \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \

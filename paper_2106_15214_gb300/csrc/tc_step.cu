@@ -329,6 +329,7 @@ tc_step_kernel(const __grid_constant__ StepMaps M, Prob<float> P, BetaParams bp,
     side.normPart = S.normPart;
     side.nparts = S.G;
     side.normK = (S.wfirst && (int)blockIdx.x < P.K) ? (int)blockIdx.x : -1;
+    side.normStride = P.K;                           // one column per block (S.G >= K)
     side.norms = P.norms;
     side.lossPart = S.lossPart;
     side.nloss = (S.wantLoss && blockIdx.x == 0) ? (S.wfirst ? S.rowUnits : S.colUnits) : 0;
@@ -336,7 +337,7 @@ tc_step_kernel(const __grid_constant__ StepMaps M, Prob<float> P, BetaParams bp,
     const SideJob* sp = (side.normK >= 0 || side.nloss > 0) ? &side : nullptr;
     const int units = S.wfirst ? S.colUnits : S.rowUnits;
     if ((int)blockIdx.x >= units) {
-      if (warp == 3) side_run(sp, lane);
+      if (warp == 3) side_run(sp, lane, P.K);
     }
     for (int u = blockIdx.x; u < units; u += S.G) {
       if (S.wfirst)
@@ -379,7 +380,7 @@ size_t step_smem(int kp, int* nopR, int* nvR, int* nopC, int* nvC, bool wfirst) 
 
 bool tc_step_supported(const Prob<float>& P, const TcMaps& m, int sms) {
   if (!m.ok || !P.sWS || P.kp > 64 || P.tcClusterS != 1 || P.tcClusterR != 1 || P.tcSK) return false;
-  if (P.K > WS_THREADS / 8) return false;            // norm reductions assume >= 8 threads per column
+  if (P.K > WS_THREADS / 8 || P.K > sms) return false;   // norm reductions: >= 8 threads, one block per column
   (void)sms;
   return true;
 }

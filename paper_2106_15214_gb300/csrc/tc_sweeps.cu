@@ -432,24 +432,26 @@ int tc_kp(int K) { return (K + 15) & ~15; }
   } while (0)
 
 cudaError_t launch_tc_row_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int dsel, int flags,
-                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st,
+                                const SideJob* side) {
   (void)bf16;
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
-  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_row(P, *maps, dsel, flags, bp, lossPart, status, st);
-  if (P.tcClusterS != 1) return cudaErrorNotSupported;   // clustered tilings need the warp-specialised kernel
+  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_row(P, *maps, dsel, flags, bp, lossPart, status, st, side);
+  if (P.tcClusterS != 1 || side) return cudaErrorNotSupported;   // clustered tilings need the warp-specialised kernel
   const size_t sm = row_smem(kp);
   const unsigned grid = (unsigned)(P.tcRowTiles * P.tcSplitS);
   NMF_TC_BK_DISPATCH(tc_row_sweep_kernel, grid, sm, P, wsel, hsel, dsel, flags, bp, lossPart, status);
 }
 
 cudaError_t launch_tc_col_sweep(const Prob<float>& P, const TcMaps* maps, int wsel, int hsel, int csel, int flags,
-                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st) {
+                                bool bf16, const BetaParams& bp, double* lossPart, int* status, cudaStream_t st,
+                                const SideJob* side) {
   (void)bf16;
   const int kp = tc_kp(P.K);
   if (kp > TC_KPMAX) return cudaErrorInvalidValue;
-  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_col(P, *maps, csel, flags, bp, lossPart, status, st);
-  if (P.tcClusterR != 1 || P.tcSK) return cudaErrorNotSupported;   // clustered / stream-K splits need the warp-specialised kernel
+  if (kp <= 64 && maps && maps->ok) return launch_tc_ws_col(P, *maps, csel, flags, bp, lossPart, status, st, side);
+  if (P.tcClusterR != 1 || P.tcSK || side) return cudaErrorNotSupported;   // clustered / stream-K splits need the warp-specialised kernel
   const size_t sm = col_smem(kp);
   const unsigned grid = (unsigned)(P.tcColTiles * P.tcSplitR);
   NMF_TC_BK_DISPATCH(tc_col_sweep_kernel, grid, sm, P, wsel, hsel, csel, flags, bp, lossPart, status);

@@ -57,7 +57,8 @@ cudaError_t prep(Kern k, size_t sm) {
 
 template <bool CHI, bool ROW>
 cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const BetaParams& bp, double* lossPart,
-                      int* status, cudaStream_t st) {
+                      int* status, cudaStream_t st, const SideJob* sidep) {
+  const SideJob side = sidep ? *sidep : SideJob();
   const int kp = P.kp;
   int nop = 0, nv = 0;
   if (!pick_rings(kp, CHI, &nop, &nv)) return cudaErrorInvalidValue;
@@ -100,12 +101,12 @@ cudaError_t launch_ws(const Prob<float>& P, const TcMaps& m, int flags, const Be
       e = prep(tc_ws_sk_kernel<BKV, CHI>, sm);                                                              \
       if (e == cudaSuccess)                                                                                \
         e = cudaLaunchKernelEx(&cfg, tc_ws_sk_kernel<BKV, CHI>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, \
-                               bp, lossPart, status);                                                      \
+                               bp, lossPart, status, side);                                                \
     } else {                                                                                               \
       e = prep(tc_ws_kernel<BKV, CHI, ROW>, sm);                                                            \
       if (e == cudaSuccess)                                                                                \
         e = cudaLaunchKernelEx(&cfg, tc_ws_kernel<BKV, CHI, ROW>, tmV, once, fa, d1, d2, useTma, nop, nv, P, flags, \
-                               bp, lossPart, status);                                                      \
+                               bp, lossPart, status, side);                                                \
     }                                                                                                      \
     break;
   switch (bp.kind) {
@@ -186,15 +187,15 @@ int tc_ws_capacity(int kp, int csize) {
 }
 
 cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, int flags, const BetaParams& bp,
-                             double* lossPart, int* status, cudaStream_t st) {
-  return dsel == OP_CHI ? launch_ws<true, true>(P, m, flags, bp, lossPart, status, st)
-                        : launch_ws<false, true>(P, m, flags, bp, lossPart, status, st);
+                             double* lossPart, int* status, cudaStream_t st, const SideJob* side) {
+  return dsel == OP_CHI ? launch_ws<true, true>(P, m, flags, bp, lossPart, status, st, side)
+                        : launch_ws<false, true>(P, m, flags, bp, lossPart, status, st, side);
 }
 
 cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, int flags, const BetaParams& bp,
-                             double* lossPart, int* status, cudaStream_t st) {
-  return csel == OP_CHI ? launch_ws<true, false>(P, m, flags, bp, lossPart, status, st)
-                        : launch_ws<false, false>(P, m, flags, bp, lossPart, status, st);
+                             double* lossPart, int* status, cudaStream_t st, const SideJob* side) {
+  return csel == OP_CHI ? launch_ws<true, false>(P, m, flags, bp, lossPart, status, st, side)
+                        : launch_ws<false, false>(P, m, flags, bp, lossPart, status, st, side);
 }
 
 }  // namespace nmf

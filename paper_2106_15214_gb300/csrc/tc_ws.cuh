@@ -132,32 +132,34 @@ struct Bars {
 
 // ROW = true: row sweep (M = 128 rows f, tiles of 32 columns n).
 // ROW = false: column sweep (M = 128 columns n, tiles of 32 rows f).
-// Optional work for the otherwise idle warp 3 of a unit (persistent step
-// kernel): the column norm of W's column `normK` from per-block partials
-// ([k][part], float), and the FP64 objective from its partials.
-struct SideJob {
-  const float* normPart;
-  int nparts;
-  int normK;                 // -1: none
-  float* norms;
-  const double* lossPart;
-  int nloss;                 // 0: none
-  double* lossOut;
-};
 
 // Run by one warp: the side job's column norm and objective (fixed-order
 // lane sums and butterfly: deterministic).
-__device__ __forceinline__ void side_run(const SideJob* side, int lane) {
-  if (side && side->normK >= 0) {
-    float sq = 0.f;
-    const float* row = side->normPart + (int64_t)side->normK * side->nparts;
-    for (int b = lane; b < side->nparts; b += 32) sq += __ldcg(&row[b]);
-    sq = warp_sum(sq);
-    if (lane == 0) side->norms[side->normK] = sqrtf(sq);
+__device__ __forceinline__ void side_run(const SideJob* side, int lane, int K) {
+  if (side && side->normPart && side->normK >= 0) {
+    for (int k = side->normK; k < K; k += side->normStride) {
+      float sq = 0.f;
+      const float* row = side->normPart + (int64_t)k * side->nparts;
+      for (int b0 = lane; b0 < side->nparts; b0 += 256) {   // loads in flight together, added in order
+        float v[8];
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = b0 + 32 * u < side->nparts ? __ldcg(&row[b0 + 32 * u]) : 0.f;
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) sq += v[u];
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) side->norms[k] = sqrtf(sq);
+    }
   }
   if (side && side->nloss > 0) {
     double sl = 0.0;
-    for (int b = lane; b < side->nloss; b += 32) sl += __ldcg(&side->lossPart[b]);
+    for (int b0 = lane; b0 < side->nloss; b0 += 256) {
+      double v[8];
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = b0 + 32 * u < side->nloss ? __ldcg(&side->lossPart[b0 + 32 * u]) : 0.0;
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) sl += v[u];
+    }
     sl = warp_sum(sl);
     if (lane == 0) side->lossOut[0] = sl;
   }
@@ -420,7 +422,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     __syncwarp();
   } else if (warp == 3) {
     // ---------------- side job (persistent step kernel) ----------------
-    side_run(side, lane);
+    side_run(side, lane, K);
   } else if (warp >= EPI_WARP0) {
     // ---------------- epilogue ----------------
     // Two groups of 8 warps take alternate tiles (group g: tiles g, g + 2, ...;
@@ -596,14 +598,13 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     __syncthreads();
     if (sl % csize == 0) {
       const int nrows = (int)(mLim - m0 < MT ? mLim - m0 : MT);
-      const int cnt = nrows * K;
       float* outP = P.rowPart + (int64_t)geo.outSlice * 2 * P.F * K + m0 * K;
       float* outQ = outP + P.F * K;
-      for (int i = tid; i < cnt; i += WS_THREADS) {
-        const int r = i / K, c = i - r * K;
-        outP[i] = stg[r * Ks + c];
-        outQ[i] = stg[MT * Ks + r * Ks + c];
-      }
+      for (int r = warp; r < nrows; r += WS_THREADS / 32)     // a warp per row, lanes along the row
+        for (int c = lane; c < K; c += 32) {
+          outP[r * K + c] = stg[r * Ks + c];
+          outQ[r * K + c] = stg[MT * Ks + r * Ks + c];
+        }
     }
   } else if (epi && sl % csize == 0) {
     const int64_t gm = m0 + mrow;
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
 tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmOnce,
              const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
              const __grid_constant__ CUtensorMap tmD2, int useTma, int nop, int nv, Prob<float> P, int flags,
-             BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
+             BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status, SideJob side) {
   pdl_trigger();
   extern __shared__ unsigned char smem_raw[];
   __shared__ Bars bars;
@@ -674,9 +675,14 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   // writes (the factor copies, the status word) are visible
   pdl_wait();
   const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
+  SideJob sj = side;
+  sj.normK = side.normPart ? (int)blockIdx.x : -1;
+  sj.normStride = gridDim.x;
+  sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
+  const bool hasSide = sj.normK >= 0 || sj.nloss > 0;
   const double l = ws_unit<BK, CHI, ROW>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status,
                                          uniform_geom<ROW>(P, blockIdx.x), skip, base, tslot, bars, s_abort, red,
-                                         nullptr, false);
+                                         hasSide ? &sj : nullptr, false);
   if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
   if ((threadIdx.x >> 5) == 2) tmem_dealloc(tslot, TM_COLS);
 }
@@ -689,7 +695,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
 tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmOnce,
                 const __grid_constant__ CUtensorMap tmFa, const __grid_constant__ CUtensorMap tmD1,
                 const __grid_constant__ CUtensorMap tmD2, int useTma, int nop, int nv, Prob<float> P, int flags,
-                BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status) {
+                BetaParams bp, double* __restrict__ lossPart, int* __restrict__ status, SideJob side) {
   pdl_trigger();
   extern __shared__ unsigned char smem_raw[];
   __shared__ Bars bars;
@@ -705,6 +711,12 @@ tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   const bool skip = *status != 0;
   const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft, G = gridDim.x;
   const int64_t a = (int64_t)blockIdx.x * T / G, b = ((int64_t)blockIdx.x + 1) * T / G;
+  SideJob sj = side;
+  sj.normK = side.normPart ? (int)blockIdx.x : -1;
+  sj.normStride = gridDim.x;
+  sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
+  const SideJob* sp = (sj.normK >= 0 || sj.nloss > 0) ? &sj : nullptr;
+  if (a >= b && (threadIdx.x >> 5) == 3) side_run(sp, threadIdx.x & 31, P.K);   // no unit: run it directly
   double l = 0.0;
   for (int64_t st = a; st < b;) {
     const int64_t nt = st / ft;
@@ -716,7 +728,8 @@ tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
     geo.s0 = (st - nt * ft) * TL;
     geo.s1 = (e - nt * ft) * TL < P.F ? (e - nt * ft) * TL : P.F;
     l += ws_unit<BK, CHI, false>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status, geo, skip, base,
-                                 tslot, bars, s_abort, red, nullptr, e < b);
+                                 tslot, bars, s_abort, red, sp, e < b);
+    sp = nullptr;                                    // with the block's first unit only
     st = e;
   }
   if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
