@@ -23,6 +23,10 @@ Readings of points the paper leaves open (each is listed again in the design doc):
     of the two updates in eq. jnt_update may be inverted (Sec. 4.1.1).
   * The gradient used by the KKT residuals (Sec. 4.1.5) is the gradient of
     D_beta(V + kappa | WH + kappa).
+  * eps (the positivity constraint W, H >= eps under which eqs. Wll, Hll pose
+    the block updates, Sec. 3.3.4): every update is clamped to eps, which is
+    the constrained argmin of the per-entry convex auxiliary function; eps = 0
+    (the default) is the unconstrained method.
 
 Parity status of each function is stated in its docstring; every function here
 is pinned by tests/test_oracle_pins.py unless it says "parity unpinned".
@@ -154,8 +158,16 @@ def chi2(X, Xt, beta: float):
     return X ** beta / Xt ** (beta - 1.0)
 
 
+def _floor(X, eps: float):
+    """Entrywise max(X, eps): over x >= eps the minimiser of a convex function
+    of one variable is its unconstrained minimiser clamped to eps, so this is
+    the argmin of the auxiliary function under the constraint X >= eps
+    (eqs. Wll, Hll). eps = 0 returns X unchanged."""
+    return np.maximum(X, eps) if eps > 0 else X
+
+
 def jmm_iteration(V, Wt, Ht, beta: float, L: int = 1, order: str = "W",
-                  kappa: float = 0.0, gamma_one: bool = False):
+                  kappa: float = 0.0, gamma_one: bool = False, eps: float = 0.0):
     """One outer iteration of Algorithm 2 (JMM) from the iterate (Wt, Ht).
 
     Vt = Wt Ht is formed once (step "Vt <- Wt Ht"); then L inner passes each
@@ -163,6 +175,7 @@ def jmm_iteration(V, Wt, Ht, beta: float, L: int = 1, order: str = "W",
     Wt and Ht, eq. jnt_update. order="H" applies the two updates in the
     inverted order (Sec. 4.1.1 remark). kappa as in Sec. 4.1.3. gamma_one=True
     is the heuristic of Sec. 3.3.3 (gamma set to 1; oracle-only variant).
+    eps > 0 clamps each update to eps (see _floor).
     Returns (W, H) before any normalisation.
     """
     g = 1.0 if gamma_one else gamma(beta)
@@ -173,11 +186,11 @@ def jmm_iteration(V, Wt, Ht, beta: float, L: int = 1, order: str = "W",
     W, H = Wt.copy(), Ht.copy()
     for _ in range(L):
         if order == "W":
-            W = Wt * ((A @ chi1(H, Ht, beta).T) / (B @ chi2(H, Ht, beta).T)) ** g
-            H = Ht * ((chi1(W, Wt, beta).T @ A) / (chi2(W, Wt, beta).T @ B)) ** g
+            W = _floor(Wt * ((A @ chi1(H, Ht, beta).T) / (B @ chi2(H, Ht, beta).T)) ** g, eps)
+            H = _floor(Ht * ((chi1(W, Wt, beta).T @ A) / (chi2(W, Wt, beta).T @ B)) ** g, eps)
         elif order == "H":
-            H = Ht * ((chi1(W, Wt, beta).T @ A) / (chi2(W, Wt, beta).T @ B)) ** g
-            W = Wt * ((A @ chi1(H, Ht, beta).T) / (B @ chi2(H, Ht, beta).T)) ** g
+            H = _floor(Ht * ((chi1(W, Wt, beta).T @ A) / (chi2(W, Wt, beta).T @ B)) ** g, eps)
+            W = _floor(Wt * ((A @ chi1(H, Ht, beta).T) / (B @ chi2(H, Ht, beta).T)) ** g, eps)
         else:
             raise ValueError(order)
     return W, H
@@ -200,22 +213,23 @@ def _bmm_h_update(V, W, H, beta, g, kappa):
 
 
 def bmm_iteration(V, W, H, beta: float, LW: int = 1, LH: int = 1, order: str = "W",
-                  kappa: float = 0.0, gamma_one: bool = False):
+                  kappa: float = 0.0, gamma_one: bool = False, eps: float = 0.0):
     """One outer iteration of Algorithm 1 (BMM): L_W updates of W with H fixed,
     then L_H updates of H with the new W fixed (eq. alt_update); the product
-    WH is recomputed before every update. order="H" swaps the two blocks."""
+    WH is recomputed before every update. order="H" swaps the two blocks;
+    eps > 0 clamps each update to eps (see _floor)."""
     g = 1.0 if gamma_one else gamma(beta)
     W, H = W.copy(), H.copy()
     if order == "W":
         for _ in range(LW):
-            W = _bmm_w_update(V, W, H, beta, g, kappa)
+            W = _floor(_bmm_w_update(V, W, H, beta, g, kappa), eps)
         for _ in range(LH):
-            H = _bmm_h_update(V, W, H, beta, g, kappa)
+            H = _floor(_bmm_h_update(V, W, H, beta, g, kappa), eps)
     elif order == "H":
         for _ in range(LH):
-            H = _bmm_h_update(V, W, H, beta, g, kappa)
+            H = _floor(_bmm_h_update(V, W, H, beta, g, kappa), eps)
         for _ in range(LW):
-            W = _bmm_w_update(V, W, H, beta, g, kappa)
+            W = _floor(_bmm_w_update(V, W, H, beta, g, kappa), eps)
     else:
         raise ValueError(order)
     return W, H
@@ -238,7 +252,8 @@ def normalize(W, H):
 
 def run(V, W0, H0, beta: float, method: str = "jmm", iters: int = 100,
         tol: float | None = None, order: str = "W", L: int = 1,
-        kappa: float = 0.0, do_normalize: bool = True, gamma_one: bool = False):
+        kappa: float = 0.0, do_normalize: bool = True, gamma_one: bool = False,
+        eps: float = 0.0):
     """Outer loop of Algorithm 1 / 2 with the Sec. 4.1.2 stopping rule.
 
     Runs at most `iters` outer iterations; with `tol`, stops at the first
@@ -252,10 +267,10 @@ def run(V, W0, H0, beta: float, method: str = "jmm", iters: int = 100,
     for _ in range(iters):
         if method == "jmm":
             W, H = jmm_iteration(V, W, H, beta, L=L, order=order, kappa=kappa,
-                                 gamma_one=gamma_one)
+                                 gamma_one=gamma_one, eps=eps)
         elif method == "bmm":
             W, H = bmm_iteration(V, W, H, beta, LW=L, LH=L, order=order,
-                                 kappa=kappa, gamma_one=gamma_one)
+                                 kappa=kappa, gamma_one=gamma_one, eps=eps)
         else:
             raise ValueError(method)
         if do_normalize:

@@ -196,6 +196,70 @@ def test_bmm_updates_are_argmins_of_block_majorisers(beta):
     assert np.allclose(H, argmin_H(V, W, W, H0, beta), rtol=1e-7)
 
 
+def _argmin_entry_above(fun, x0, eps):
+    """Minimiser over [eps, inf) of a 1-D convex function: eps when the
+    numerical derivative there is >= 0, else the root of the derivative
+    above eps (searched in log space)."""
+    def dfun(t):
+        w = np.exp(t)
+        h = 1e-6 * w
+        return (fun(w + h) - fun(w - h)) / (2 * h)
+    if dfun(np.log(eps)) >= 0:
+        return eps
+    return float(np.exp(optimize.brentq(dfun, np.log(eps), np.log(x0) + 12, xtol=1e-13, rtol=1e-13)))
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1.5, 3.0])
+@pytest.mark.parametrize("order", ["W", "H"])
+def test_jmm_with_floor_is_the_constrained_argmin(beta, order):
+    """With eps > 0 each half-update is the argmin of G over entries >= eps
+    (the positivity constraint of eqs. Wll, Hll), and the second half uses the
+    constrained first half. eps is set inside the range of the first
+    unconstrained update so that part of it is clamped."""
+    V, Wt, Ht = tiny(9)
+    W0, H0 = O.jmm_iteration(V, Wt, Ht, beta, order=order)
+    eps = float(np.median(W0 if order == "W" else H0))
+    W, H = O.jmm_iteration(V, Wt, Ht, beta, order=order, eps=eps)
+
+    def constrained_W(Hfix):
+        out = np.empty_like(Wt)
+        for f in range(Wt.shape[0]):
+            for k in range(Wt.shape[1]):
+                def g(w):
+                    Wm = Wt.copy()
+                    Wm[f, k] = w
+                    return O.auxiliary_G(V, Wm, Hfix, Wt, Ht, beta)
+                out[f, k] = _argmin_entry_above(g, Wt[f, k], eps)
+        return out
+
+    def constrained_H(Wfix):
+        out = np.empty_like(Ht)
+        for k in range(Ht.shape[0]):
+            for n in range(Ht.shape[1]):
+                def g(h):
+                    Hm = Ht.copy()
+                    Hm[k, n] = h
+                    return O.auxiliary_G(V, Wfix, Hm, Wt, Ht, beta)
+                out[k, n] = _argmin_entry_above(g, Ht[k, n], eps)
+        return out
+
+    if order == "W":
+        Wb = constrained_W(Ht)
+        assert (Wb == eps).sum() >= Wt.size // 3          # the constraint is active
+        assert np.allclose(W, Wb, rtol=1e-7)
+        assert np.allclose(H, constrained_H(W), rtol=1e-7)
+    else:
+        Hb = constrained_H(Wt)
+        assert (Hb == eps).sum() >= Ht.size // 3
+        assert np.allclose(H, Hb, rtol=1e-7)
+        assert np.allclose(W, constrained_W(H), rtol=1e-7)
+    # monotone descent survives the constraint while the iterate stays
+    # feasible (no normalisation, which could rescale entries below eps)
+    D = O.run(V, np.maximum(Wt, eps), np.maximum(Ht, eps), beta, iters=30, order=order, eps=eps,
+              do_normalize=False)[2]
+    assert np.all(np.diff(D) <= 1e-12 * D[:-1])
+
+
 def test_jmm_with_kappa_is_jmm_on_shifted_problem():
     """kappa acts as a (K+1)-th constant component (Sec. 4.1.3): JMM on
     (V + kappa) with W augmented by a column of kappa and H by a row of ones,
