@@ -79,7 +79,8 @@ typedef struct nmf_ctx nmf_ctx; /* opaque */
  * (eq. beta-div; any finite beta). F, N, K >= 1, else NMF_EINVAL. Allocates
  * scratch lazily on the first step. Default options: NMF_FP32, NMF_W_FIRST,
  * normalisation on (Sec. 4.1.2), kappa = 0, deterministic reductions, legacy
- * default stream, one sub-iteration (L = 1). */
+ * default stream, one sub-iteration (L = 1), the precision's default floor
+ * (nmf_set_floor). */
 nmf_status nmf_create(int64_t F, int64_t N, int32_t K, double beta, nmf_ctx** out);
 
 /* Creates a context holding `count` independent problems of sizes F[i] x N[i]
@@ -98,6 +99,15 @@ nmf_status nmf_batch_create(int32_t count, const int64_t* F, const int64_t* N,
 nmf_status nmf_set_options(nmf_ctx* ctx, nmf_precision precision, nmf_order order,
                            int normalize, double kappa, int deterministic,
                            void* cuda_stream);
+
+/* Floor eps on W and H: every update is clamped to max(update, eps), the
+ * minimiser of the auxiliary function under the positivity constraint
+ * W, H >= eps of eqs. Wll / Hll (Sec. 3.3.4). eps < 0 restores the default:
+ * 0 for NMF_FP64, 1e-30 for single precision (there, entries that the updates
+ * drive toward zero would underflow after some hundreds of iterations at
+ * beta < 1 and turn chi's ratio into 0 / 0). eps = 0 is the unconstrained
+ * method. NaN or Inf: NMF_EINVAL. */
+nmf_status nmf_set_floor(nmf_ctx* ctx, double eps);
 
 /* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
  * Algorithm 1) per outer iteration. */

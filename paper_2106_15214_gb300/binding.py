@@ -19,7 +19,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 ORDERS = {"W": W_FIRST, "H": H_FIRST, "auto": ORDER_AUTO}
 
 EXPORTS = [
-    "nmf_create", "nmf_batch_create", "nmf_set_options", "nmf_set_subiterations", "nmf_set_dense",
+    "nmf_create", "nmf_batch_create", "nmf_set_options", "nmf_set_floor", "nmf_set_subiterations", "nmf_set_dense",
     "nmf_set_csr", "nmf_set_factors", "nmf_batch_set_packed", "nmf_step_joint",
     "nmf_step_alternating", "nmf_loss", "nmf_grad", "nmf_kkt", "nmf_batch_get_losses",
     "nmf_get_status", "nmf_step_joint_host", "nmf_set_timing", "nmf_get_timing", "nmf_reset_timing",
@@ -48,6 +48,7 @@ def _declare(lib):
         "nmf_batch_create": [I32, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32), D,
                              ctypes.POINTER(P)],
         "nmf_set_options": [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, ctypes.c_int, P],
+        "nmf_set_floor": [P, D],
         "nmf_set_subiterations": [P, I32],
         "nmf_set_dense": [P, P, I64],
         "nmf_set_csr": [P, I64, P, P, P],
@@ -135,7 +136,7 @@ class NMF:
     contiguous); W and H are updated in place by the step calls."""
 
     def __init__(self, F, N, K, beta, precision="fp32", order="W", normalize=True, kappa=0.0,
-                 L=1, stream=None):
+                 L=1, stream=None, floor=None):
         lib = load()
         self._lib = lib
         self.F, self.N, self.K, self.beta = int(F), int(N), int(K), float(beta)
@@ -149,7 +150,13 @@ class NMF:
         self.set_options()
         if L != 1:
             check(lib.nmf_set_subiterations(self._ctx, int(L)), "nmf_set_subiterations")
+        if floor is not None:
+            self.set_floor(floor)
         self._keep = []
+
+    def set_floor(self, eps):
+        """Clamp every update to eps (nmf_set_floor); eps < 0 restores the default."""
+        check(self._lib.nmf_set_floor(self._ctx, float(eps)), "nmf_set_floor")
 
     def set_options(self, stream=None):
         s = ctypes.c_void_p(stream) if stream is not None else _stream()

@@ -27,6 +27,7 @@ struct nmf_ctx {
   nmf_order order = NMF_W_FIRST;
   int normalize = 1;
   double kappa = 0.0;
+  double floorEps = -1.0;          // < 0: the precision's default (floor_of)
   int deterministic = 1;
   cudaStream_t stream = nullptr;
   int L = 1;
@@ -476,11 +477,21 @@ nmf_status prepare(nmf_ctx* c) {
 }
 
 
+// Floor on W and H (every update is clamped to it): the one set by
+// nmf_set_floor, else 0 in FP64 and 1e-30 in single precision, where
+// entries that MU drives toward zero would otherwise underflow after some
+// hundreds of iterations (beta < 1) and make chi's ratio X / Xt = 0 / 0.
+double floor_of(const nmf_ctx* c) {
+  if (c->floorEps >= 0.0) return c->floorEps;
+  return c->prec == NMF_FP64 ? 0.0 : 1e-30;
+}
+
 BetaParams beta_params(const nmf_ctx* c) {
   BetaParams bp;
   bp.beta = c->beta;
   bp.gamma = gamma_of(c->beta);
   bp.kappa = c->kappa;
+  bp.floor = floor_of(c);
   bp.kind = beta_kind(c->beta);
   fill_series(bp);
   return bp;
@@ -991,6 +1002,13 @@ nmf_status nmf_set_options(nmf_ctx* c, nmf_precision precision, nmf_order order,
   c->kappa = kappa;
   c->deterministic = deterministic ? 1 : 0;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return NMF_OK;
+}
+
+nmf_status nmf_set_floor(nmf_ctx* c, double eps) {
+  if (!c || std::isnan(eps) || std::isinf(eps)) return NMF_EINVAL;
+  invalidate_graphs(c);
+  c->floorEps = eps < 0.0 ? -1.0 : eps;
   return NMF_OK;
 }
 

@@ -35,6 +35,7 @@ struct BetaParams {
   double beta;
   double gamma;
   double kappa;
+  double floor = 0.0;  // every update is clamped to >= floor (0: off)
   int kind;
   float series[7];  // Taylor coefficients of phi_beta(u) for u^2 .. u^8 (fill_series)
 };
@@ -157,6 +158,13 @@ __device__ __forceinline__ void ab_terms(T v, T vt, T bm2, T& A, T& B) {
     B = vt * p;
   }
 }
+
+// An update clamped to eps: over x >= eps the minimiser of the per-entry
+// convex auxiliary function is the unconstrained one clamped to eps (the
+// positivity constraint W, H >= eps of eqs. Wll, Hll). NaN stays NaN, so the
+// non-finite check still sees it; eps = 0 leaves x unchanged.
+template <typename T>
+__device__ __forceinline__ T apply_floor(T x, T eps) { return x < eps ? eps : x; }
 
 // (num / den)^gamma
 template <int BK, typename T>

@@ -126,6 +126,7 @@ extern "C" nmf_status nmf_loss_noalloc(int64_t F, int64_t N, int32_t K, double b
   bp.beta = beta;
   bp.gamma = gamma_of(beta);
   bp.kappa = kappa;
+  bp.floor = 0.0;
   bp.kind = beta_kind(beta);
   fill_series(bp);
   if (precision == NMF_FP64)

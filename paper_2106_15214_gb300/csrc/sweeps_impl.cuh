@@ -396,7 +396,7 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
       gout[idx] = den - num;
     } else {
       const T base = basesel == SEL_TILDE ? P.Wt[idx] : P.W[idx];
-      const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+      const T x = apply_floor(base * mu_ratio<BK, T>(num, den, (T)bp.gamma), (T)bp.floor);
       if (!isfinite(x)) atomicExch(status, 4);
       P.W[idx] = x;
       sq = x * x;
@@ -463,15 +463,15 @@ cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
     T num, den;
     int slices = tc ? P.tcR : P.R;
     if (tc && P.tcSK) {                                  // stream-K: this column tile's own count
-      const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft;
-      slices = sk_slices((idx % P.N) / 128, ft, T, P.tcSKBlocks);
+      const int64_t ft = (P.F + 31) / 32, steps = (int64_t)P.tcColTiles * ft;
+      slices = sk_slices((idx % P.N) / 128, ft, steps, P.tcSKBlocks);
     }
     sum_slices(P.colPart + idx, 2 * KN, KN, slices, num, den);
     if (mode == EPI_GRAD) {
       gout[idx] = den - num;
     } else {
       const T base = basesel == SEL_TILDE ? P.Ht[idx] : P.H[idx];
-      const T x = base * mu_ratio<BK, T>(num, den, (T)bp.gamma);
+      const T x = apply_floor(base * mu_ratio<BK, T>(num, den, (T)bp.gamma), (T)bp.floor);
       if (!isfinite(x)) atomicExch(status, 4);
       if (want_chi) {
         T c1, c2;
@@ -556,7 +556,7 @@ cols_epilogue_vec4_kernel(const Prob<float>* __restrict__ probs, int basesel, in
       bool finite = true;
       #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float x = bs[j] * mu_ratio<BK, float>(nv[j], dv[j], (float)bp.gamma);
+        const float x = apply_floor(bs[j] * mu_ratio<BK, float>(nv[j], dv[j], (float)bp.gamma), (float)bp.floor);
         finite = finite && isfinite(x);
         if (want_chi) chi_terms<BK, float>(x, ht[j], (float)bp.beta, c1[j], c2[j]);
         y[j] = ((fz.flags & FUSE_NORM_APPLY) && nk > 0.f) ? x * nk : x;

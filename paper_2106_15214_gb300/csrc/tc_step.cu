@@ -177,7 +177,7 @@ __device__ void phase_rows_epi(const Prob<float>& P, const BetaParams& bp, const
     float sq = 0.f;
     if (inside && sub == 0) {
       const float wt = __ldcg(P.Wt + idx);
-      const float x = wt * mu_ratio<BK, float>(num, den, (float)bp.gamma);
+      const float x = apply_floor(wt * mu_ratio<BK, float>(num, den, (float)bp.gamma), (float)bp.floor);
       if (!isfinite(x)) atomicExch(S.status, 4);
       P.W[idx] = x;
       sq = x * x;
@@ -213,7 +213,7 @@ __device__ void phase_cols_epi(const Prob<float>& P, const BetaParams& bp, const
     float num, den;
     slice_sums(P.colPart + idx, KN, P.tcR, num, den);
     const float ht = __ldcg(P.Ht + idx);
-    const float x = ht * mu_ratio<BK, float>(num, den, (float)bp.gamma);
+    const float x = apply_floor(ht * mu_ratio<BK, float>(num, den, (float)bp.gamma), (float)bp.floor);
     if (!isfinite(x)) atomicExch(S.status, 4);
     const int64_t k = idx / P.N;
     if (wantChi) {

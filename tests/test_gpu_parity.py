@@ -33,11 +33,11 @@ def to_dev(a, prec):
 
 
 def gpu_run(lib, V, W0, H0, beta, prec="fp64", method="jmm", iters=1, order="W", L=1, kappa=0.0,
-            normalize=True):
+            normalize=True, floor=None):
     from paper_2106_15214_gb300.binding import NMF
     F, N = V.shape
     K = W0.shape[1]
-    m = NMF(F, N, K, beta, precision=prec, order=order, normalize=normalize, kappa=kappa, L=L)
+    m = NMF(F, N, K, beta, precision=prec, order=order, normalize=normalize, kappa=kappa, L=L, floor=floor)
     Vd, Wd, Hd = to_dev(V, prec), to_dev(W0, prec), to_dev(H0, prec)
     m.set_dense(Vd)
     m.set_factors(Wd, Hd)
@@ -46,9 +46,9 @@ def gpu_run(lib, V, W0, H0, beta, prec="fp64", method="jmm", iters=1, order="W",
     return out
 
 
-def oracle_run(V, W0, H0, beta, method="jmm", iters=1, order="W", L=1, kappa=0.0, normalize=True):
+def oracle_run(V, W0, H0, beta, method="jmm", iters=1, order="W", L=1, kappa=0.0, normalize=True, eps=0.0):
     W, H, losses = O.run(V, W0, H0, beta, method=method, iters=iters, order=order, L=L, kappa=kappa,
-                         do_normalize=normalize)
+                         do_normalize=normalize, eps=eps)
     return W, H, losses
 
 
@@ -245,3 +245,42 @@ def test_graph_replay_matches_eager_bitwise(lib, prec):
             assert losses[i] == l
     for W, H, _ in outs:
         assert np.array_equal(W, Wd.cpu().numpy()) and np.array_equal(H, Hd.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("method", ["jmm", "bmm"])
+@pytest.mark.parametrize("order", ["W", "H"])
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_floor_matches_oracle(lib, prec, method, order, beta):
+    """nmf_set_floor: every update is clamped to eps (the constraint W, H >= eps
+    of eqs. Wll, Hll). eps is the median of the first raw update of the block
+    updated first, so about half of it is clamped; 10 iterations."""
+    V, W0, H0 = problem(90, 130, 6, seed=11)
+    it = O.jmm_iteration if method == "jmm" else O.bmm_iteration
+    W1, H1 = it(V, W0, H0, beta, order=order)
+    eps = float(np.median(W1 if order == "W" else H1))
+    W, H, loss, _ = gpu_run(lib, V, W0, H0, beta, prec, method, iters=10, order=order, floor=eps)
+    Wo, Ho, lo = oracle_run(V, W0, H0, beta, method, iters=10, order=order, eps=eps)
+    rtol = 1e-11 if prec == "fp64" else 2e-3
+    assert_close(W, Wo, rtol, "W")
+    assert_close(H, Ho, rtol, "H")
+    assert loss == pytest.approx(lo[9], rel=1e-11 if prec == "fp64" else 1e-5)
+
+
+def test_floor_defaults_and_errors(lib):
+    """Default floor: 0 in FP64 (the unconstrained method), 1e-30 in single
+    precision; eps < 0 restores the default; NaN / Inf are rejected."""
+    from paper_2106_15214_gb300.binding import NMF, NMFError
+    V, W0, H0 = problem(30, 40, 3, seed=12)
+    m = NMF(30, 40, 3, 1.0, precision="fp64")
+    for bad in (float("nan"), float("inf")):
+        with pytest.raises(NMFError):
+            m.set_floor(bad)
+    m.set_floor(0.5)
+    m.set_floor(-1.0)
+    Vd, Wd, Hd = to_dev(V, "fp64"), to_dev(W0, "fp64"), to_dev(H0, "fp64")
+    m.set_dense(Vd)
+    m.set_factors(Wd, Hd)
+    m.step_joint(3)
+    Wo, Ho, _ = oracle_run(V, W0, H0, 1.0, iters=3)
+    assert_close(Wd.cpu().numpy(), Wo, 1e-12, "W (default floor, FP64)")

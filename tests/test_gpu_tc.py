@@ -33,11 +33,11 @@ def problem(F, N, K, seed=0):
     return V, W0, H0
 
 
-def run_tc(V, W0, H0, beta, method="jmm", iters=1, order="W", L=1, kappa=0.0, prec="tf32"):
+def run_tc(V, W0, H0, beta, method="jmm", iters=1, order="W", L=1, kappa=0.0, prec="tf32", floor=None):
     from paper_2106_15214_gb300.binding import NMF
     F, N = V.shape
     K = W0.shape[1]
-    m = NMF(F, N, K, beta, precision=prec, order=order, L=L, kappa=kappa)
+    m = NMF(F, N, K, beta, precision=prec, order=order, L=L, kappa=kappa, floor=floor)
     Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
     m.set_dense(Vd)
     m.set_factors(Wd, Hd)
@@ -207,3 +207,40 @@ def test_tf32_stream_k_column_sweep(lib, monkeypatch, order, method, K):
     W1, H1, loss1, _ = run_tc(V, W0, H0, 1.0, method, 2, order)
     assert maxrel(W, W1) < 1e-3 and maxrel(H, H1) < 1e-3
     assert loss == pytest.approx(loss1, rel=1e-4)
+
+
+@pytest.mark.parametrize("order", ["W", "H"])
+@pytest.mark.parametrize("K", [20, 49])
+@pytest.mark.parametrize("N", [300, 20000])
+def test_tf32_floor_matches_oracle(lib, order, K, N):
+    """The floor in the tensor-core path's epilogues (the 16-byte vector H
+    epilogue and the stream-K column sweep at N = 20000): one JMM iteration
+    with eps at the median of the raw first update."""
+    V, W0, H0 = problem(200, N, K, seed=13)
+    W1, H1 = O.jmm_iteration(V, W0, H0, 0.0, order=order)
+    eps = float(np.median(W1 if order == "W" else H1))
+    W, H, _, _ = run_tc(V, W0, H0, 0.0, "jmm", 1, order, floor=eps)
+    Wo, Ho, _ = O.run(V, W0, H0, 0.0, iters=1, order=order, eps=eps)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+
+
+@pytest.mark.parametrize("prec", ["tf32", "fp32"])
+def test_long_itakura_saito_run_stays_finite(lib, prec):
+    """Itakura-Saito JMM on spectrogram-shaped data drives entries of H toward
+    zero geometrically (about 1e-40 after 700 iterations in FP32 at N = 1000);
+    without a floor they underflow and chi's ratio becomes 0 / 0. The default
+    single-precision floor (1e-30) keeps 1200 iterations finite and descending."""
+    from paper_2106_15214_gb300.binding import NMF
+    p = inputs.dense_is_spectrogram(N=1000)
+    F, N, K = p.shape
+    m = NMF(F, N, K, 0.0, precision=prec, order="H")
+    Vd, Wd, Hd = dev(p.V), dev(p.W0), dev(p.H0)
+    m.set_dense(Vd)
+    m.set_factors(Wd, Hd)
+    losses = [m.step_joint(100) for _ in range(12)]
+    assert all(np.isfinite(losses))
+    assert all(b <= a * (1 + 1e-4) for a, b in zip(losses, losses[1:]))
+    W, H = Wd.double().cpu().numpy(), Hd.double().cpu().numpy()
+    assert np.isfinite(W).all() and np.isfinite(H).all()
+    assert H.min() < 1e-20          # the run did reach the regime where FP32 would underflow
