@@ -175,6 +175,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t byte
 // 2-D TMA tile load (x = inner coordinate in elements, y = row); completes
 // `bytes` of transaction count on the mbarrier. x * element size must be a
 // multiple of 16 bytes.
+// Brings a tensor map (a kernel parameter) into the TMA unit's descriptor
+// cache ahead of its first copy.
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" :: "l"(tmap) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* m) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"

@@ -189,14 +189,68 @@ __device__ __forceinline__ UnitGeom uniform_geom(const Prob<float>& P, int unit)
   return g;
 }
 
+// Initialises the unit's barriers (one thread; a __syncthreads must follow).
+__device__ __forceinline__ void ws_init_bars(Bars& bars, int nop, int nv, int useTma) {
+  for (int s = 0; s < nop; ++s) {
+    mbar_init(&bars.opfull[s], 1u);
+    mbar_init(&bars.opempty[s], 1u);
+  }
+  for (int s = 0; s < nv; ++s) {
+    mbar_init(&bars.vfull[s], useTma ? 1u : 32u);
+    mbar_init(&bars.vempty[s], EPI_THREADS / 64);   // the 8 warps of the group that reads the tile
+  }
+  for (int b = 0; b < NFA; ++b) {
+    mbar_init(&bars.fafull[b], 1u);
+    mbar_init(&bars.fafree[b], 1u);
+  }
+  for (int b = 0; b < 2; ++b) {
+    mbar_init(&bars.tfull[b], 1u);
+    mbar_init(&bars.vafree[b], 1u);
+    mbar_init(&bars.abready[b], EPI_THREADS / 64);
+    mbar_init(&bars.abfree[b], 1u);
+  }
+  mbar_init(&bars.once, 1u);
+  mbar_init(&bars.onceT, 4u);                      // epilogue warps 4-7 after moving it to TMEM
+  mbar_init(&bars.done, 1u);
+  fence_mbar_init();
+}
+
+// Streamed tiles of a unit and the V tiles that may be loaded before the
+// previous kernel has finished (V is never written by the step's kernels):
+// the first min(nv, tiles) through TMA.
+__device__ __forceinline__ int ws_tiles(const Prob<float>& P, bool row, const UnitGeom& g) {
+  const int64_t sLim = row ? P.N : P.F;
+  return g.s0 < sLim ? (int)((g.s1 - g.s0 + TL - 1) / TL) : 0;
+}
+
+// Run by the V producer warp before the dependency wait: issues V tiles
+// 0 .. n - 1 of the unit into ring slots 0 .. n - 1 (one elected lane).
+template <bool ROW>
+__device__ __forceinline__ void ws_v_issue(const CUtensorMap& tmV, const Prob<float>& P, const UnitGeom& g, int n,
+                                           unsigned char* vring, Bars& bars) {
+  if (elect_one()) {
+    const int m0 = g.mt * MT;
+    for (int t = 0; t < n; ++t) {
+      const int c0 = (int)(g.s0 + (int64_t)t * TL);
+      mbar_arrive_expect_tx(&bars.vfull[t], TB);
+      if (ROW) tma_load_2d(vring + t * TB, &tmV, c0, m0, &bars.vfull[t]);
+      else tma_load_2d(vring + t * TB, &tmV, m0, c0, &bars.vfull[t]);
+    }
+  }
+  __syncwarp();
+}
+
 // Returns the unit's objective partial (valid in thread 0; 0 without SWEEP_LOSS).
+// barsReady: the caller initialised the barriers; vPre: V tiles the caller
+// already issued (ws_v_issue), which are waited for even when the unit skips.
 template <int BK, bool CHI, bool ROW>
 __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensorMap& tmOnce, const CUtensorMap& tmFa,
                                           const CUtensorMap& tmD1, const CUtensorMap& tmD2, int useTma, int nop,
                                           int nv, const Prob<float>& P, int flags, const BetaParams& bp,
                                           int* __restrict__ status, const UnitGeom& geo, bool skip,
                                           unsigned char* base, uint32_t tbase, Bars& bars, volatile int& s_abort,
-                                          double* red, const SideJob* side, bool reuse) {
+                                          double* red, const SideJob* side, bool reuse, bool barsReady = false,
+                                          int vPre = 0) {
   const int K = P.K, kp = (K + 15) & ~15, na = (kp + 31) / 32;
   const WsLayout L = ws_layout(kp, CHI, nop, nv);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -206,11 +260,10 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
   const int mt = geo.mt, sl = geo.sl;
   const int64_t m0 = (int64_t)mt * MT;
   const int64_t mLim = ROW ? P.F : P.N;
-  const int64_t sLim = ROW ? P.N : P.F;
   const int64_t s0 = geo.s0;
   const int64_t s1 = geo.s1;
   // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
-  const int ntilesGeom = s0 < sLim ? (int)((s1 - s0 + TL - 1) / TL) : 0;
+  const int ntilesGeom = ws_tiles(P, ROW, geo);
   const bool wantLoss = flags & SWEEP_LOSS;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
   const uint32_t dBytes = (uint32_t)kp * 128u;
@@ -218,28 +271,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
 
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < nop; ++s) {
-      mbar_init(&bars.opfull[s], 1u);
-      mbar_init(&bars.opempty[s], 1u);
-    }
-    for (int s = 0; s < nv; ++s) {
-      mbar_init(&bars.vfull[s], useTma ? 1u : 32u);
-      mbar_init(&bars.vempty[s], EPI_THREADS / 64);   // the 8 warps of the group that reads the tile
-    }
-    for (int b = 0; b < NFA; ++b) {
-      mbar_init(&bars.fafull[b], 1u);
-      mbar_init(&bars.fafree[b], 1u);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&bars.tfull[b], 1u);
-      mbar_init(&bars.vafree[b], 1u);
-      mbar_init(&bars.abready[b], EPI_THREADS / 64);
-      mbar_init(&bars.abfree[b], 1u);
-    }
-    mbar_init(&bars.once, 1u);
-    mbar_init(&bars.onceT, 4u);                      // epilogue warps 4-7 after moving it to TMEM
-    mbar_init(&bars.done, 1u);
-    fence_mbar_init();
+    if (!barsReady) ws_init_bars(bars, nop, nv, useTma);
   }
   __syncthreads();
   const int ntiles = skip ? 0 : ntilesGeom;
@@ -288,9 +320,13 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     }
   } else if (warp == 1) {
     // ---------------- V producer: TMA from an elected lane, else cp.async from the warp ----------------
-    int st = 0;
-    uint32_t ph = 0;
-    for (int t = 0; t < ntiles; ++t) {
+    // tiles 0 .. vPre - 1 were issued before the dependency wait; a unit
+    // that skips still waits for them (no copy may land after the block ends)
+    for (int t = ntiles; t < vPre; ++t)
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars.vfull[t], 0u, 100000000ull))) break;
+    int st = vPre < nv ? vPre : 0;
+    uint32_t ph = vPre < nv ? 0u : 1u;
+    for (int t = vPre; t < ntiles; ++t) {
       const int64_t c0 = s0 + (int64_t)t * TL;
       if (t >= nv && !__all_sync(0xffffffffu, role_wait(&bars.vempty[st], ph ^ 1u, &s_abort, status))) break;
       unsigned char* vb = base + L.v0 + st * TB;
@@ -329,12 +365,17 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     }
   } else if (warp == 2) {
     // ---------------- MMA issuer ----------------
-    // The warp polls two queues converged; an elected lane issues each batch:
-    //   MMA1 of batch j (Vt of 4 tiles, N = 128, into TMEM buffer j & 1) once
-    //   its B operand is loaded and MMA2/3 of batch j - 2 (which read their A
-    //   tiles from the same buffer) have completed;
-    //   MMA2/3 of tile t2 once the epilogue has written its A/B tiles and the
-    //   tile's B operands are loaded.
+    // A fixed schedule; the warp sleeps in each wait (mbarrier try_wait with a
+    // suspend hint) and one elected lane issues:
+    //   MMA1 of batches 0 and 1 (Vt of 4 tiles each, N = 128, into TMEM
+    //   buffer j & 1);
+    //   per tile t2: MMA2/3 once the epilogue has written its A/B tiles and
+    //   the tile's B operands are loaded; after the first tile of batch
+    //   j - 1, MMA1 of batch j (its buffer's previous batch, j - 2, has been
+    //   issued completely one tile earlier, so its completion is near).
+    // A sleeping warp takes no issue slots from the epilogue warps that share
+    // its scheduler, and wakes when the barrier completes; a polling loop
+    // over several queues measured one tile-period of reaction time.
     // Every A operand is read from TMEM, every B operand from shared memory.
     // Descriptors are built once; an operand at byte offset o is the base
     // descriptor plus o / 16 (the start-address field, bits 0-13, cannot carry
@@ -343,80 +384,62 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     const uint64_t dFa = desc_sw128(smem_u32(base + L.fa0));
     const uint64_t dOp = desc_sw128(smem_u32(base + L.op0));
     const uint32_t fa16 = L.fa_bytes >> 4, op16 = L.op_bytes >> 4, d2_16 = L.off_d2 >> 4;
-    int j1 = 0, t2 = 0, so2 = 0;
+    int j1 = 0, so2 = 0;
     uint32_t po2 = 0;
-    uint64_t idle0 = 0;
     bool ok = ntiles > 0 && role_wait(&bars.onceT, 0u, &s_abort, status);
     ok = __all_sync(0xffffffffu, ok);
-    fence_after_sync();
-    while (ok && t2 < ntiles) {
-      bool prog = false;
-      bool can1 = j1 < nbatch && mbar_test(&bars.fafull[j1 & (NFA - 1)], (uint32_t)(j1 / NFA) & 1u) &&
-                  (j1 < 2 || mbar_test(&bars.vafree[j1 & 1], (uint32_t)((j1 - 2) >> 1) & 1u));
-      can1 = __shfl_sync(0xffffffffu, can1, 0);
-      if (can1) {
-        fence_after_sync();
-        const uint64_t db0 = dFa + (uint64_t)((j1 & (NFA - 1)) * fa16);
-        const uint32_t dv = tbase + 128u * (j1 & 1);
-        if (elect_one()) {
-          #pragma unroll
-          for (int ks = 0; ks < 8; ++ks)
-            if (ks < kp / 8) {
-              const uint32_t k0 = (uint32_t)ks * 8u;
-              mma_tf32_ts(dv, tbase + TM_ONCE + k0, db0 + (((k0 >> 5) * TB + (k0 & 31u) * 4u) >> 4), id_v, ks > 0);
-            }
-          mma_commit(&bars.tfull[j1 & 1]);
-          mma_commit(&bars.fafree[j1 & (NFA - 1)]);
-        }
-        __syncwarp();
-        ++j1;
-        prog = true;
-      }
-      bool can2 = t2 < j1 * BT && mbar_test(&bars.abready[t2 & 1], (uint32_t)(t2 >> 1) & 1u) &&
-                  mbar_test(&bars.opfull[so2], po2);
-      can2 = __shfl_sync(0xffffffffu, can2, 0);
-      if (can2) {
-        fence_after_sync();
-        const int b = t2 & 1;
-        const uint32_t tA = tbase + 128u * ((t2 >> 2) & 1) + 32u * (t2 & 3), tB = tbase + TM_B + 32u * b;
-        const uint64_t dD1 = dOp + (uint64_t)(so2 * op16), dD2 = dD1 + d2_16;
-        const bool lastOfBatch = (t2 & (BT - 1)) == BT - 1 || t2 == ntiles - 1;
-        if (elect_one()) {
-          #pragma unroll
-          for (int ks = 0; ks < TL / 8; ++ks) {
-            const uint32_t acc = (t2 > 0 || ks > 0) ? 1u : 0u;
-            mma_tf32_ts(t_acc1, tA + 8u * ks, dD1 + 2u * ks, id_acc, acc);   // 32 bytes along K
-            mma_tf32_ts(t_acc2, tB + 8u * ks, dD2 + 2u * ks, id_acc, acc);
+    // MMA1 of batch j: Fa tile loaded, TMEM buffer j & 1 free (batch j - 2's MMA2/3 complete)
+    auto mma1 = [&](int j) -> bool {
+      const int fs = j & (NFA - 1);
+      if (!__all_sync(0xffffffffu, role_wait(&bars.fafull[fs], (uint32_t)(j / NFA) & 1u, &s_abort, status)))
+        return false;
+      if (j >= 2 &&
+          !__all_sync(0xffffffffu, role_wait(&bars.vafree[j & 1], (uint32_t)((j - 2) >> 1) & 1u, &s_abort, status)))
+        return false;
+      fence_after_sync();
+      const uint64_t db0 = dFa + (uint64_t)(fs * fa16);
+      const uint32_t dv = tbase + 128u * (j & 1);
+      if (elect_one()) {
+        #pragma unroll
+        for (int ks = 0; ks < 8; ++ks)
+          if (ks < kp / 8) {
+            const uint32_t k0 = (uint32_t)ks * 8u;
+            mma_tf32_ts(dv, tbase + TM_ONCE + k0, db0 + (((k0 >> 5) * TB + (k0 & 31u) * 4u) >> 4), id_v, ks > 0);
           }
-          mma_commit(&bars.abfree[b]);
-          mma_commit(&bars.opempty[so2]);
-          if (lastOfBatch) mma_commit(&bars.vafree[(t2 >> 2) & 1]);
-        }
-        __syncwarp();
-        ++t2;
-        if (++so2 == nop) {
-          so2 = 0;
-          po2 ^= 1u;
-        }
-        prog = true;
+        mma_commit(&bars.tfull[j & 1]);
+        mma_commit(&bars.fafree[fs]);
       }
-      if (prog) {
-        idle0 = 0;
-      } else {
-        const bool ab = s_abort != 0;
-        const uint64_t now = globaltimer_ns();
-        if (!idle0) idle0 = now;
-        bool quit = ab || now - idle0 > 1000000000ull;
-        quit = __shfl_sync(0xffffffffu, quit, 0);
-        if (quit) {
-          if (!ab && lane == 0) {
-            s_abort = 1;
-            atomicExch(status, ETIMEOUT);
-          }
-          break;
+      __syncwarp();
+      return true;
+    };
+    if (ok) ok = mma1(j1++);
+    if (ok && j1 < nbatch) ok = mma1(j1++);
+    for (int t2 = 0; ok && t2 < ntiles; ++t2) {
+      if (!__all_sync(0xffffffffu, role_wait(&bars.abready[t2 & 1], (uint32_t)(t2 >> 1) & 1u, &s_abort, status)))
+        break;
+      if (!__all_sync(0xffffffffu, role_wait(&bars.opfull[so2], po2, &s_abort, status))) break;
+      fence_after_sync();
+      const int b = t2 & 1;
+      const uint32_t tA = tbase + 128u * ((t2 >> 2) & 1) + 32u * (t2 & 3), tB = tbase + TM_B + 32u * b;
+      const uint64_t dD1 = dOp + (uint64_t)(so2 * op16), dD2 = dD1 + d2_16;
+      const bool lastOfBatch = (t2 & (BT - 1)) == BT - 1 || t2 == ntiles - 1;
+      if (elect_one()) {
+        #pragma unroll
+        for (int ks = 0; ks < TL / 8; ++ks) {
+          const uint32_t acc = (t2 > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32_ts(t_acc1, tA + 8u * ks, dD1 + 2u * ks, id_acc, acc);   // 32 bytes along K
+          mma_tf32_ts(t_acc2, tB + 8u * ks, dD2 + 2u * ks, id_acc, acc);
         }
-        __nanosleep(32);
+        mma_commit(&bars.abfree[b]);
+        mma_commit(&bars.opempty[so2]);
+        if (lastOfBatch) mma_commit(&bars.vafree[(t2 >> 2) & 1]);
       }
+      __syncwarp();
+      if (++so2 == nop) {
+        so2 = 0;
+        po2 ^= 1u;
+      }
+      if (j1 < nbatch && t2 == BT * (j1 - 1)) ok = mma1(j1++);
     }
     if (elect_one()) mma_commit(&bars.done);
     __syncwarp();
@@ -666,23 +689,42 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   __shared__ uint32_t tslot;
   __shared__ volatile int s_abort;
   __shared__ double red[32];
+  __shared__ int s_skip;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  if ((threadIdx.x >> 5) == 2) tmem_alloc(&tslot, TM_COLS);
+  const int warp = threadIdx.x >> 5;
+  const UnitGeom geo = uniform_geom<ROW>(P, blockIdx.x);
+  const int vPre = useTma ? min(nv, ws_tiles(P, ROW, geo)) : 0;
+  // Everything up to the dependency wait overlaps the previous kernel's
+  // tail: TMEM allocation, barrier initialisation, the tensor maps' fetch
+  // and the first V tiles (V is read-only for the whole step).
+  if (warp == 2) tmem_alloc(&tslot, TM_COLS);
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tmV);
+    prefetch_tmap(&tmOnce);
+    prefetch_tmap(&tmFa);
+    prefetch_tmap(&tmD1);
+    prefetch_tmap(&tmD2);
+    ws_init_bars(bars, nop, nv, useTma);
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  // everything above overlaps the previous kernel's tail; from here on its
-  // writes (the factor copies, the status word) are visible
+  if (warp == 1 && vPre > 0)
+    ws_v_issue<ROW>(tmV, P, geo, vPre, base + ws_layout((P.K + 15) & ~15, CHI, nop, nv).v0, bars);
+  // from here on the previous kernel's writes (the factor copies, the status
+  // word) are visible; the status is read once for the whole block
   pdl_wait();
-  const bool skip = *status != 0;   // read once; the block still runs to the end (cluster barriers)
+  if (threadIdx.x == 0) s_skip = *status != 0;
+  __syncthreads();
+  const bool skip = s_skip != 0;    // the block still runs to the end (cluster barriers)
   SideJob sj = side;
   sj.normK = side.normPart ? (int)blockIdx.x : -1;
   sj.normStride = gridDim.x;
   sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
   const bool hasSide = sj.normK >= 0 || sj.nloss > 0;
-  const double l = ws_unit<BK, CHI, ROW>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status,
-                                         uniform_geom<ROW>(P, blockIdx.x), skip, base, tslot, bars, s_abort, red,
-                                         hasSide ? &sj : nullptr, false);
+  const double l = ws_unit<BK, CHI, ROW>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status, geo,
+                                         skip, base, tslot, bars, s_abort, red, hasSide ? &sj : nullptr, false, true,
+                                         vPre);
   if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
   if ((threadIdx.x >> 5) == 2) tmem_dealloc(tslot, TM_COLS);
 }
@@ -702,34 +744,60 @@ tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   __shared__ uint32_t tslot;
   __shared__ volatile int s_abort;
   __shared__ double red[32];
+  __shared__ int s_skip;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  if ((threadIdx.x >> 5) == 2) tmem_alloc(&tslot, TM_COLS);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  pdl_wait();
-  const bool skip = *status != 0;
+  const int warp = threadIdx.x >> 5;
   const int64_t ft = (P.F + 31) / 32, T = (int64_t)P.tcColTiles * ft, G = gridDim.x;
   const int64_t a = (int64_t)blockIdx.x * T / G, b = ((int64_t)blockIdx.x + 1) * T / G;
-  SideJob sj = side;
-  sj.normK = side.normPart ? (int)blockIdx.x : -1;
-  sj.normStride = gridDim.x;
-  sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
-  const SideJob* sp = (sj.normK >= 0 || sj.nloss > 0) ? &sj : nullptr;
-  if (a >= b && (threadIdx.x >> 5) == 3) side_run(sp, threadIdx.x & 31, P.K);   // no unit: run it directly
-  double l = 0.0;
-  for (int64_t st = a; st < b;) {
+  // unit of tile steps [st, e): the steps of column tile st / ft inside [a, b)
+  auto unit_of = [&](int64_t st, int64_t* e) {
     const int64_t nt = st / ft;
-    const int64_t e = (nt + 1) * ft < b ? (nt + 1) * ft : b;
+    *e = (nt + 1) * ft < b ? (nt + 1) * ft : b;
     UnitGeom geo;
     geo.mt = (int)nt;
     geo.sl = 0;
     geo.outSlice = (int)(blockIdx.x - sk_block_of(nt * ft, T, G));
     geo.s0 = (st - nt * ft) * TL;
-    geo.s1 = (e - nt * ft) * TL < P.F ? (e - nt * ft) * TL : P.F;
+    geo.s1 = (*e - nt * ft) * TL < P.F ? (*e - nt * ft) * TL : P.F;
+    return geo;
+  };
+  int64_t e0 = a;
+  const UnitGeom geo0 = a < b ? unit_of(a, &e0) : UnitGeom();
+  const int vPre = useTma && a < b ? min(nv, ws_tiles(P, false, geo0)) : 0;
+  // as in tc_ws_kernel: the first unit's set-up and V tiles before the wait
+  if (warp == 2) tmem_alloc(&tslot, TM_COLS);
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tmV);
+    prefetch_tmap(&tmOnce);
+    prefetch_tmap(&tmFa);
+    prefetch_tmap(&tmD1);
+    prefetch_tmap(&tmD2);
+    ws_init_bars(bars, nop, nv, useTma);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 1 && vPre > 0)
+    ws_v_issue<false>(tmV, P, geo0, vPre, base + ws_layout((P.K + 15) & ~15, CHI, nop, nv).v0, bars);
+  pdl_wait();
+  if (threadIdx.x == 0) s_skip = *status != 0;
+  __syncthreads();
+  const bool skip = s_skip != 0;
+  SideJob sj = side;
+  sj.normK = side.normPart ? (int)blockIdx.x : -1;
+  sj.normStride = gridDim.x;
+  sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
+  const SideJob* sp = (sj.normK >= 0 || sj.nloss > 0) ? &sj : nullptr;
+  if (a >= b && warp == 3) side_run(sp, threadIdx.x & 31, P.K);   // no unit: run it directly
+  double l = 0.0;
+  bool first = true;
+  for (int64_t st = a; st < b;) {
+    int64_t e = e0;
+    const UnitGeom geo = first ? geo0 : unit_of(st, &e);
     l += ws_unit<BK, CHI, false>(tmV, tmOnce, tmFa, tmD1, tmD2, useTma, nop, nv, P, flags, bp, status, geo, skip, base,
-                                 tslot, bars, s_abort, red, sp, e < b);
+                                 tslot, bars, s_abort, red, sp, e < b, first, first ? vPre : 0);
     sp = nullptr;                                    // with the block's first unit only
+    first = false;
     st = e;
   }
   if ((flags & SWEEP_LOSS) && threadIdx.x == 0) lossPart[blockIdx.x] = l;
