@@ -36,10 +36,18 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of each kernel as it now stands, keyed by (workload, precision,
+# order, kernel name as in `kernels`); ncu flushes caches before each captured
+# launch. Sources and commands: the traffic summaries under profiles/. An
+# entry is removed when its kernel changes.
+NCU_TRAFFIC = {}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="faces", choices=sorted(WORKLOADS))
@@ -97,7 +105,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, csv line)
+        self.window = None       # (t0, t1) of the timed region, time.monotonic()
 
     def __enter__(self):
         try:
@@ -106,13 +115,23 @@ class ClockSampler:
                  "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: wait (bounded) for its first sample
+            t_end = time.monotonic() + 5.0
+            while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def begin(self):
+        self.window = (time.monotonic(), None)
+
+    def end(self):
+        self.window = (self.window[0], time.monotonic())
 
     def __exit__(self, *a):
         if self.proc:
@@ -125,7 +144,14 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window and self.window[1] is not None:
+            # samples taken during the timed region (plus one sampling period, the line's delivery delay)
+            inside = [ln for t, ln in lines if self.window[0] <= t <= self.window[1] + 0.05]
+            lines = inside or [ln for _, ln in lines]
+        else:
+            lines = [ln for _, ln in lines]
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -306,17 +332,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier(world)
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
     # Timed region: K steps enqueued back to back. Each step computes the
     # objective into device memory (no host round trip inside the region);
     # the L2 flush runs between steps, outside the step's events. About 2 ms
     # of untimed flushes are queued first so the host runs ahead of the GPU
     # and a host-side pause cannot leave the GPU idle inside a step's events.
+    # The clock sampler is started (and has delivered a sample) before it.
     import gc
-    gc.disable()
     with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        gc.disable()
+        clk.begin()
         for j in range(30):
             flush.fill_(float(-j))
         for i in range(args.steps):
@@ -325,8 +353,9 @@ def run_ours(args):
             m.step_joint_async(loss_dev[i:i + 1])
             ends[i].record(stream)
         torch.cuda.synchronize()
-    gc.enable()
-    barrier(world)
+        clk.end()
+        gc.enable()
+        barrier(world)
     wall = time.perf_counter() - wall0
     st = m._lib.nmf_get_status(m._ctx)
     if st != 0:
@@ -368,7 +397,8 @@ def run_ours(args):
             return None
         ach = ab / per_launch_s / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "algorithmic_bytes": ab,
+                "frac": ach / peak, "traffic": NCU_TRAFFIC.get((args.workload, precision, args.order, name)),
+                "algorithmic_bytes": ab,
                 "avg_launch_us": per_launch_s * 1e6, "launches": n, "peak_source": peak_src,
                 "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
 
