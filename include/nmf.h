@@ -128,7 +128,12 @@ nmf_status nmf_set_dense(nmf_ctx* ctx, const void* V_dev, int64_t ldv);
 nmf_status nmf_set_csr(nmf_ctx* ctx, int64_t nnz, const int32_t* rowptr,
                        const int32_t* col, const float* val);
 
-/* Borrows the factors (device): W F x K, H K x N, updated in place. */
+/* Borrows the factors (device): W F x K, H K x N, updated in place. A step
+ * may leave in the context the operand copies of the W and H it returns
+ * (NMF_TF32, W first), which the next step then uses instead of copying them
+ * again: after writing W or H in place between steps, call nmf_set_factors
+ * again (same pointers are fine), which drops those copies and clears the
+ * status word. */
 nmf_status nmf_set_factors(nmf_ctx* ctx, void* W_dev, void* H_dev);
 
 /* Batched contexts: V, W, H of every problem packed back to back, problem i

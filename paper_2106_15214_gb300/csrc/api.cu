@@ -28,6 +28,10 @@ struct nmf_ctx {
   int normalize = 1;
   double kappa = 0.0;
   double floorEps = -1.0;          // < 0: the precision's default (floor_of)
+  // The operand copies (tilde and TF32 copies) of the current W, H were made
+  // by the last kernel of the previous step (W first, tensor cores): the next
+  // step skips its copies kernel. Cleared by every call that may change W, H.
+  bool copiesValid = false;
   int deterministic = 1;
   cudaStream_t stream = nullptr;
   int L = 1;
@@ -86,6 +90,7 @@ struct nmf_ctx {
     cudaGraphExec_t exec = nullptr;
     Timer::Sink sink;
     const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // data captured with
+    bool copiesAfter = false;      // copiesValid after the captured step
   };
   std::vector<GraphEntry> graphs;
   std::vector<uint64_t> seenKeys;
@@ -513,6 +518,19 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   // (warp-specialised kernels), so the epilogues skip the full-precision chi
   int tci = tc ? 1 : 0;
   if (tc && c->tcmaps.ok && c->count == 1 && c->hpf[0].kp <= 64) tci = 2;
+  // single problems fold the objective's finalisation and the normalisation
+  // into the epilogues (EpiFuse); batched contexts use the separate kernels
+  const bool fuse = !c->batched;
+  const bool norm = c->normalize != 0;
+  // W first on the warp-specialised path: the iteration's last kernel also
+  // makes the next iteration's copies, so that iteration (in this call or,
+  // while nothing changes W and H in between, the next call) skips the copies
+  // kernel. NMF_TC_FUSE_COPIES=0 keeps the separate copies kernel.
+  const char* fcEnv = std::getenv("NMF_TC_FUSE_COPIES");
+  const bool fuseCopies = !(fcEnv && fcEnv[0] == '0') && tci == 2 && joint && L == 1 && fuse && norm && wfirst &&
+                          c->hpf[0].sWS;
+  bool haveCopies = fuseCopies && c->copiesValid;
+  c->copiesValid = false;
   auto row_sweep = [&](int wsel, int hsel, int dsel, int flags, const SideJob* side = nullptr) -> nmf_status {
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
@@ -547,9 +565,6 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     }
     return NMF_OK;
   };
-  // single problems fold the objective's finalisation and the normalisation
-  // into the epilogues (EpiFuse); batched contexts use the separate kernels
-  const bool fuse = !c->batched;
   const int rowGrid = tc ? c->hpf[0].tcRowTiles * c->hpf[0].tcSplitS : pl.totRow;
   const int colGrid = tc ? (c->hpf[0].tcSK ? c->hpf[0].tcSKBlocks : c->hpf[0].tcColTiles * c->hpf[0].tcSplitR)
                        : pl.totCol;
@@ -578,7 +593,6 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     })));
     return basesel == SEL_CUR ? shadows(2) : NMF_OK;
   };
-  const bool norm = c->normalize != 0;
   // NMF_TC_STEP=1: one persistent cooperative launch per iteration
   // (tc_step.cu) where it applies. Off by default: on the 361 x 2429 and
   // 513 x 20000 workloads it measured slower than the per-kernel sequence
@@ -611,8 +625,10 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     const int lossFlag = (fuse && lossHere) ? FUSE_LOSS : 0;
     if (tci && c->count == 1 && c->hpf[0].sWS) {
       if constexpr (std::is_same<T, float>::value)
-        NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
-                     [&] { return launch_tc_copies<float>(c->hpf[0], true, true, true, status, st); }));
+        if (!haveCopies)
+          NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
+                       [&] { return launch_tc_copies<float>(c->hpf[0], true, true, true, status, st); }));
+      haveCopies = false;            // this iteration's updates change W and H
     } else {
       NMF_CU(timed(&c->timer, st, "begin_iteration", 1, [&] { return launch_begin_iteration<T>(pl, status, st); }));
     }
@@ -636,7 +652,14 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
         NMF_TRY(rows_epi(SEL_TILDE, 1, FUSE_NORM_PART | FUSE_NO_FINALIZE));
         NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C, &sj));
-        NMF_TRY(cols_epi(SEL_TILDE, 0, FUSE_NORM_APPLY));
+        if (fuseCopies) {
+          if constexpr (std::is_same<T, float>::value)
+            NMF_CU(timed(&c->timer, st, "cols_epilogue", 1,
+                         [&] { return launch_cols_next<float>(pl, c->hpf[0], bp, status, st); }));
+          haveCopies = true;
+        } else {
+          NMF_TRY(cols_epi(SEL_TILDE, 0, FUSE_NORM_APPLY));
+        }
       } else {
         NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
         NMF_TRY(cols_epi(SEL_TILDE, 1, 0));
@@ -697,6 +720,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     if (norm && !normDone) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
   }
   c->lossFused = fuse;
+  c->copiesValid = haveCopies;
   if (wantLoss) c->lossPrefix = (wfirst ? 0 : 1) + (tc ? 2 : 0);
   return NMF_OK;
 }
@@ -727,6 +751,7 @@ nmf_status complete_readback(nmf_ctx* c, bool readLoss, double* loss_out) {
   const int cnt = c->count;
   const int hs = *reinterpret_cast<int*>(c->h_pinned + cnt + 1);
   if (hs != 0) {
+    c->copiesValid = false;
     const size_t es = c->sparse ? 4 : esize(c);
     void* W = c->batched ? c->Wp : c->W;
     void* H = c->batched ? c->Hp : c->H;
@@ -804,10 +829,12 @@ uint64_t step_key(const nmf_ctx* c, bool joint, int iters, bool wantLoss, bool r
   k = k * 4 + (joint ? 1 : 0) + (wantLoss ? 2 : 0);
   k = k * 2 + (c->timer.on ? 1 : 0);
   k = k * 2 + (readback ? 1 : 0);
+  k = k * 2 + (c->copiesValid ? 1 : 0);
   return k;
 }
 
 void invalidate_graphs(nmf_ctx* c) {
+  c->copiesValid = false;
   for (auto& g : c->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& p : g.sink.pairs) { c->timer.pool.push_back(p.a); c->timer.pool.push_back(p.b); }
@@ -841,6 +868,7 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
   cudaGraph_t graph = nullptr;
   bool ok = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   nmf_status st = ok ? enqueue_step(c, joint, iters, wantLoss, readback) : NMF_ECUDA;
+  e.copiesAfter = c->copiesValid;
   if (ok) ok = cudaStreamEndCapture(c->gs, &graph) == cudaSuccess && st == NMF_OK && graph;
   if (ok) ok = cudaGraphInstantiate(&e.exec, graph, 0) == cudaSuccess;
   if (graph) cudaGraphDestroy(graph);
@@ -850,6 +878,7 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
     cudaGetLastError();
     for (auto& p : e.sink.pairs) { c->timer.pool.push_back(p.a); c->timer.pool.push_back(p.b); }
     c->useGraphs = false;
+    c->copiesValid = false;       // the captured step never ran
     return nullptr;
   }
   c->graphs.push_back(std::move(e));
@@ -858,6 +887,7 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
 
 // loss_dev != nullptr: asynchronous step; the loss goes to that device buffer.
 nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* loss_out, double* loss_dev) {
+  c->copiesValid = g.copiesAfter;
   NMF_CU(cudaEventRecord(c->evIn, c->stream));
   NMF_CU(cudaStreamWaitEvent(c->gs, c->evIn, 0));
   NMF_CU(cudaGraphLaunch(g.exec, c->gs));
@@ -1089,6 +1119,7 @@ nmf_status nmf_step_alternating_async(nmf_ctx* c, int32_t iters, double* loss_de
 nmf_status nmf_loss(nmf_ctx* c, double* out_host) {
   if (!c || !out_host) return NMF_EINVAL;
   if (!data_ready(c)) return NMF_ENOTREADY;
+  c->copiesValid = false;          // the evaluation runs in FP32 and may rebuild scratch
   nmf_precision keep = c->prec;
   if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
   nmf_status s = prepare(c);
@@ -1116,6 +1147,7 @@ nmf_status nmf_grad(nmf_ctx* c, void* gW_dev, void* gH_dev, double* loss_out) {
   if (!c || !gW_dev || !gH_dev) return NMF_EINVAL;
   if (c->batched) return NMF_EUNSUPPORTED;
   if (!data_ready(c)) return NMF_ENOTREADY;
+  c->copiesValid = false;
   nmf_precision keep = c->prec;
   if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
   nmf_status s = prepare(c);
@@ -1155,6 +1187,7 @@ nmf_status nmf_kkt(nmf_ctx* c, double* resW, double* resH) {
   if (!c || !resW || !resH) return NMF_EINVAL;
   if (c->batched) return NMF_EUNSUPPORTED;
   if (!data_ready(c)) return NMF_ENOTREADY;
+  c->copiesValid = false;
   nmf_precision keep = c->prec;
   if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;
   nmf_status s = prepare(c);
@@ -1231,6 +1264,7 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
   NMF_CU(cudaMemcpyAsync(c->stageH, H_host, es * c->elemsH, cudaMemcpyHostToDevice, c->stream));
   c->W = c->stageW; c->H = c->stageH;
   c->tableDirty = true;
+  c->copiesValid = false;          // W, H come from the host
   nmf_status s = step(c, true, iters, loss_out);
   if (s == NMF_OK || s == NMF_ENONFINITE) {
     nmf_status s2 = cu(cudaMemcpyAsync(W_host, c->stageW, es * c->elemsW, cudaMemcpyDeviceToHost, c->stream));
@@ -1241,6 +1275,7 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
   c->V = keepV; c->W = keepW; c->H = keepH; c->ldv = keepLd;
   c->tableDirty = true;
   c->vDirty = true;
+  c->copiesValid = false;          // the copies are of the staged W, H
   return s;
 }
 

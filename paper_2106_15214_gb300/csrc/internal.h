@@ -194,6 +194,12 @@ inline int rows_epilogue_lanes(const Plan<T>& pl, int tc) {
 // `tilde` the W~, H~ copies too (the begin of a tensor-core iteration).
 template <typename T>
 cudaError_t launch_tc_copies(const Prob<T>& P, bool doW, bool doH, bool tilde, const int* status, cudaStream_t st);
+// The last H epilogue of a W-first tensor-core iteration (normalisation on)
+// fused with the next iteration's copies (what launch_tc_copies with tilde
+// would make from the final W, H); single problem.
+template <typename T>
+cudaError_t launch_cols_next(const Plan<T>& pl, const Prob<T>& hp, const BetaParams& bp, int* status,
+                             cudaStream_t st);
 // Launch with programmatic stream serialization (the kernel calls pdl_wait()
 // before reading anything its predecessor wrote).
 template <typename... KArgs, typename... Args>

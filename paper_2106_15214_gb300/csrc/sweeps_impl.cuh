@@ -22,6 +22,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace nmf {
@@ -580,6 +582,126 @@ cols_epilogue_vec4_kernel(const Prob<float>* __restrict__ probs, int basesel, in
   if (fz.flags & FUSE_LOSS) last_block_finalize<float>(fz, P, totQ, nullptr);
 }
 
+// The iteration's last H epilogue (W first, normalisation on, one
+// tensor-core problem) fused with the next iteration's operand copies.
+// Blocks [0, nt) take a tile of 8 rows k x 32 V columns n of H each (a warp
+// per row, V consecutive entries per thread; V = 4 needs N % 4 == 0 and H
+// 16-byte aligned): slice sums, the MU update, the floor, the norm scaling,
+// then H, Ht, the TF32 copy sHS and, through a shared-memory transpose, the
+// TF32 copy sHT (N x ks: 32 bytes of each of the tile's rows n). Blocks
+// [nt, ...) divide W's columns by the norms and write W, Wt, sWS and sWT.
+// Every value is the one the H epilogue followed by the copies kernel would
+// produce (same operations, same order).
+template <int BK, int V>
+__global__ void __launch_bounds__(EW)
+cols_next_kernel(const Prob<float>* __restrict__ probs, BetaParams bp, int* __restrict__ status, int nt) {
+  pdl_trigger();
+  pdl_wait();
+  if (*status) return;
+  constexpr int TK = EW / 32;                          // rows k per tile
+  constexpr int TN = 32 * V;                           // columns n per tile
+  __shared__ float tile[TN][TK + 1];                   // odd row stride: few bank conflicts
+  const Prob<float> P = probs[0];
+  const int b = blockIdx.x;
+  if (b >= nt) {                                       // W /= norms and W's copies
+    const int64_t idx = (int64_t)(b - nt) * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const int64_t f = idx / P.K, k = idx - f * P.K;
+      const float nk = P.norms[k];
+      const float w = nk > 0.f ? P.W[idx] / nk : P.W[idx];
+      P.W[idx] = w;
+      P.Wt[idx] = w;
+      const float r = tf32_round(w);
+      P.sWS[f * P.ks + k] = r;
+      P.sWT[k * P.Fp + f] = r;
+    }
+    return;
+  }
+  const int ntN = (int)((P.N + TN - 1) / TN);
+  const int64_t n0 = (int64_t)(b % ntN) * TN;
+  const int k0 = (b / ntN) * TK;
+  const int lane = threadIdx.x & 31, kk = threadIdx.x >> 5;
+  const int64_t KN = (int64_t)P.K * P.N, n = n0 + (int64_t)V * lane;
+  const int k = k0 + kk;
+  if (n < P.N && k < P.K) {
+    int slices = P.tcR;
+    if (P.tcSK) {                                      // stream-K: this column tile's own count
+      const int64_t ft = (P.F + 31) / 32, steps = (int64_t)P.tcColTiles * ft;
+      slices = sk_slices(n / 128, ft, steps, P.tcSKBlocks);
+    }
+    const int64_t idx = (int64_t)k * P.N + n;
+    const float nk = P.norms[k];
+    float y[V];
+    bool finite = true;
+    if (V == 1) {
+      float num, den;
+      sum_slices(P.colPart + idx, 2 * KN, KN, slices, num, den);
+      const float x = apply_floor(P.Ht[idx] * mu_ratio<BK, float>(num, den, (float)bp.gamma), (float)bp.floor);
+      finite = isfinite(x);
+      y[0] = nk > 0.f ? x * nk : x;
+      P.H[idx] = y[0];
+      P.Ht[idx] = y[0];
+    } else {
+      float4 num = make_float4(0.f, 0.f, 0.f, 0.f), den = num;
+      const float* part = P.colPart + idx;
+      for (int s0 = 0; s0 < slices; s0 += 4) {         // four slices' loads in flight, added in slice order
+        float4 vn[4], vd[4];
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int sl = s0 + u;
+          vn[u] = sl < slices ? *reinterpret_cast<const float4*>(part + (int64_t)sl * 2 * KN) : make_float4(0.f, 0.f, 0.f, 0.f);
+          vd[u] = sl < slices ? *reinterpret_cast<const float4*>(part + (int64_t)sl * 2 * KN + KN)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          num.x += vn[u].x; num.y += vn[u].y; num.z += vn[u].z; num.w += vn[u].w;
+          den.x += vd[u].x; den.y += vd[u].y; den.z += vd[u].z; den.w += vd[u].w;
+        }
+      }
+      const float nv[4] = {num.x, num.y, num.z, num.w}, dv[4] = {den.x, den.y, den.z, den.w};
+      const float4 ht4 = *reinterpret_cast<const float4*>(P.Ht + idx);
+      const float ht[4] = {ht4.x, ht4.y, ht4.z, ht4.w};
+      #pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const float x = apply_floor(ht[j] * mu_ratio<BK, float>(nv[j], dv[j], (float)bp.gamma), (float)bp.floor);
+        finite = finite && isfinite(x);
+        y[j] = nk > 0.f ? x * nk : x;
+      }
+      const float4 y4 = make_float4(y[0], y[1], y[2], y[3]);
+      *reinterpret_cast<float4*>(P.H + idx) = y4;
+      *reinterpret_cast<float4*>(P.Ht + idx) = y4;
+    }
+    if (!finite) atomicExch(status, 4);
+    float r[V];
+    #pragma unroll
+    for (int j = 0; j < V; ++j) {
+      r[j] = tf32_round(y[j]);
+      tile[V * lane + j][kk] = r[j];
+    }
+    if (V == 1) P.sHS[(int64_t)k * P.Np + n] = r[0];
+    else *reinterpret_cast<float4*>(P.sHS + (int64_t)k * P.Np + n) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+  __syncthreads();
+  if (V == 1) {
+    const int nl = threadIdx.x / TK, kt = threadIdx.x % TK;   // 32 rows n x TK columns k
+    if (n0 + nl < P.N && k0 + kt < P.K) P.sHT[(n0 + nl) * P.ks + k0 + kt] = tile[nl][kt];
+  } else {
+    // 128 rows n x 8 columns k: two 16-byte pieces per row (k0 and ks are
+    // multiples of 8, so each piece is aligned); columns k >= K stay zero
+    const int nl = threadIdx.x >> 1, h = threadIdx.x & 1;
+    if (n0 + nl < P.N) {
+      float4 v = make_float4(tile[nl][4 * h], tile[nl][4 * h + 1], tile[nl][4 * h + 2], tile[nl][4 * h + 3]);
+      const int kb = k0 + 4 * h;
+      if (kb + 0 >= P.K) v.x = 0.f;
+      if (kb + 1 >= P.K) v.y = 0.f;
+      if (kb + 2 >= P.K) v.z = 0.f;
+      if (kb + 3 >= P.K) v.w = 0.f;
+      if (kb < P.K) *reinterpret_cast<float4*>(P.sHT + (n0 + nl) * P.ks + kb) = v;
+    }
+  }
+}
+
 // Normalisation of one problem from the W epilogue's norm partials
 // ([K][nparts]): every block reduces them itself (R threads per column, then
 // a fixed-order sum: the same norms in every block), then blocks [0, totW)
@@ -981,6 +1103,39 @@ cudaError_t launch_normalize_parts(const Plan<T>& pl, const T* normPart, int npa
 }
 
 template <typename T>
+cudaError_t launch_cols_next(const Plan<T>& pl, const Prob<T>& hp, const BetaParams& bp, int* status,
+                             cudaStream_t st) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (pl.count != 1 || hp.K > KMAX || !hp.sWS || !hp.sHT || hp.ks % 8 != 0) return cudaErrorInvalidValue;
+    const bool v4 = pl.colVec4;
+    const int64_t tn = v4 ? 128 : 32;
+    const int nt = (int)(((hp.N + tn - 1) / tn) * ((hp.K + EW / 32 - 1) / (EW / 32)));
+    const dim3 grid((unsigned)(nt + (hp.F * hp.K + EW - 1) / EW));
+    const Prob<float>* probs = pl.d_probs;
+    cudaError_t le = cudaErrorInvalidValue;
+#define NMF_NEXT_CASE(BKV)                                                                                  \
+  case BKV:                                                                                                 \
+    le = v4 ? launch_pdl(cols_next_kernel<BKV, 4>, grid, dim3(EW), 0, st, probs, bp, status, nt)            \
+            : launch_pdl(cols_next_kernel<BKV, 1>, grid, dim3(EW), 0, st, probs, bp, status, nt);           \
+    break;
+    switch (bp.kind) {
+      NMF_NEXT_CASE(BK_IS)
+      NMF_NEXT_CASE(BK_KL)
+      NMF_NEXT_CASE(BK_EUC)
+      NMF_NEXT_CASE(BK_B15)
+      default:
+        le = v4 ? launch_pdl(cols_next_kernel<BK_GENERAL, 4>, grid, dim3(EW), 0, st, probs, bp, status, nt)
+                : launch_pdl(cols_next_kernel<BK_GENERAL, 1>, grid, dim3(EW), 0, st, probs, bp, status, nt);
+    }
+#undef NMF_NEXT_CASE
+    if (le != cudaSuccess) return le;
+    return cudaGetLastError();
+  }
+}
+
+template <typename T>
 cudaError_t launch_begin_iteration(const Plan<T>& pl, const int* status, cudaStream_t st) {
   {
     const cudaError_t le_ = launch_pdl(begin_iteration_kernel<T>, dim3(pl.totW + pl.totH), dim3(EW), 0, st, pl.d_probs, pl.count, pl.d_prefW, pl.totW, pl.d_prefH, status);
@@ -1027,6 +1182,7 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_normalize_parts<T>(const Plan<T>&, const T*, int, const int*, cudaStream_t); \
   template cudaError_t launch_tc_copies<T>(const Prob<T>&, bool, bool, bool, const int*, cudaStream_t); \
+  template cudaError_t launch_cols_next<T>(const Plan<T>&, const Prob<T>&, const BetaParams&, int*, cudaStream_t); \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \
                                      double*, cudaStream_t);                                       \

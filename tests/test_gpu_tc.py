@@ -244,3 +244,62 @@ def test_long_itakura_saito_run_stays_finite(lib, prec):
     W, H = Wd.double().cpu().numpy(), Hd.double().cpu().numpy()
     assert np.isfinite(W).all() and np.isfinite(H).all()
     assert H.min() < 1e-20          # the run did reach the regime where FP32 would underflow
+
+
+@pytest.mark.parametrize("F,N,K", [(200, 300, 20), (361, 2429, 49), (150, 1030, 33), (513, 20000, 20)])
+@pytest.mark.parametrize("beta", [0.0, 1.0, 2.0])
+def test_fused_next_copies_match_the_copies_kernel(lib, monkeypatch, F, N, K, beta):
+    """W first: the iteration's last kernel also makes the next iteration's
+    operand copies, and the next step (or iteration) skips the copies kernel.
+    Bitwise the same iterates and objectives as with the separate copies
+    kernel (NMF_TC_FUSE_COPIES=0), across calls (graph capture and replay from
+    the third call on) and within a multi-iteration call."""
+    V, W0, H0 = problem(F, N, K, seed=21)
+
+    from paper_2106_15214_gb300.binding import NMF
+    out = []
+    for fuse in ("1", "0"):
+        monkeypatch.setenv("NMF_TC_FUSE_COPIES", fuse)
+        m = NMF(F, N, K, beta, precision="tf32", order="W")
+        Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
+        m.set_dense(Vd)
+        m.set_factors(Wd, Hd)
+        losses = [m.step_joint(1) for _ in range(5)] + [m.step_joint(3)]
+        out.append((Wd.cpu().numpy(), Hd.cpu().numpy(), losses))
+    (Wa, Ha, la), (Wb, Hb, lb) = out
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+    assert la == lb
+
+
+def test_fused_copies_are_dropped_by_set_factors_and_other_calls(lib):
+    """After an in-place write of W followed by nmf_set_factors, and around
+    nmf_loss and alternating steps, a context with fused copies gives the same
+    iterates as a fresh context started from the same W, H."""
+    from paper_2106_15214_gb300.binding import NMF
+    import torch
+    V, W0, H0 = problem(240, 700, 24, seed=22)
+    m = NMF(240, 700, 24, 1.0, precision="tf32", order="W")
+    Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
+    m.set_dense(Vd)
+    m.set_factors(Wd, Hd)
+    for _ in range(3):
+        m.step_joint(1)
+    Wd.mul_(1.5)                                 # in-place change of W ...
+    m.set_factors(Wd, Hd)                        # ... announced to the context
+    W1, H1 = Wd.clone(), Hd.clone()
+    m.step_joint(1)
+    m.loss()
+    m.step_joint(1)
+    m.step_alternating(1)
+    m.step_joint(2)
+    f = NMF(240, 700, 24, 1.0, precision="tf32", order="W")
+    W2, H2 = W1.clone(), H1.clone()
+    f.set_dense(Vd)
+    f.set_factors(W2, H2)
+    f.step_joint(1)
+    f.loss()
+    f.step_joint(1)
+    f.step_alternating(1)
+    f.step_joint(2)
+    torch.cuda.synchronize()
+    assert torch.equal(Wd, W2) and torch.equal(Hd, H2)
