@@ -41,7 +41,16 @@ WORKLOADS = {
 # order, kernel name as in `kernels`); ncu flushes caches before each captured
 # launch. Sources and commands: the traffic summaries under profiles/. An
 # entry is removed when its kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("faces", "tf32", "W", "tc_row_sweep"): 4918272,
+    ("faces", "tf32", "W", "rows_epilogue"): 5478656,
+    ("faces", "tf32", "W", "tc_col_sweep"): 4515328,
+    ("faces", "tf32", "W", "cols_epilogue"): 6276864,
+    ("spectrogram", "tf32", "W", "tc_row_sweep"): 46301440,
+    ("spectrogram", "tf32", "W", "rows_epilogue"): 2534400,
+    ("spectrogram", "tf32", "W", "tc_col_sweep"): 43899136 + 512,
+    ("spectrogram", "tf32", "W", "cols_epilogue"): 7788288,
+}
 
 
 def parse():
@@ -213,7 +222,9 @@ def algorithmic_bytes(kernel, F, N, K, esize=4):
         "tc_col_sweep": V + 3 * FK + KN + 2 * KN,
         # P, Q and W~ in; W, chi_1(W), chi_2(W) and their two tensor-core copies out
         "rows_epilogue": 8 * FK,
-        "cols_epilogue": 8 * KN,
+        # W first, the iteration's last kernel: Hn, Hd and H~ in; H, H~ and the
+        # two tensor-core copies of H out; W in; W, W~ and W's two copies out
+        "cols_epilogue": 7 * KN + 5 * FK,
         # W, H in; W~, H~ and two tensor-core copies of each out
         "begin_iteration": 4 * (FK + KN),
         "normalize": 2 * (FK + KN),
