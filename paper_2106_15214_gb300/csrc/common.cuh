@@ -313,6 +313,54 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Fixed-order block sum (any blockDim multiple of 32, <= 1024); result valid in thread 0.
+// Float-float (double-single) accumulation: a value carried as hi + lo,
+// about 44 significant bits, with single-precision operations only (FP64
+// runs at a small fraction of the FP32 rate on GB300). two_sum is Knuth's
+// error-free transformation: s + e equals a + b exactly (round-to-nearest
+// adds, no reassociation).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (bhi, blo), renormalised so that |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo = 0.f) {
+  float s, e;
+  two_sum(hi, bhi, s, e);
+  e += lo + blo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Block sum of float-float values: lane and warp butterflies and the
+// cross-warp sum in float-float, converted to double once (thread 0 returns
+// it; the butterflies run in a fixed order, so the result is deterministic).
+__device__ __forceinline__ double block_sum_ff(float hi, float lo, float2* sh /* >= 32 */) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, oh, ol);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (int)((blockDim.x + 31) >> 5);
+  __syncthreads();
+  if (l == 0) sh[w] = make_float2(hi, lo);
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    const float2 v = l < nw ? sh[l] : make_float2(0.f, 0.f);
+    hi = v.x;
+    lo = v.y;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      ff_add(hi, lo, oh, ol);
+    }
+    if (l == 0) r = (double)hi + (double)lo;
+  }
+  return r;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
   v = warp_sum(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;

@@ -277,7 +277,9 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
   const int ntiles = skip ? 0 : ntilesGeom;
   const int nbatch = (ntiles + BT - 1) / BT;
   const uint32_t t_acc1 = tbase + TM_ACC1, t_acc2 = tbase + TM_ACC2;   // P | Hn, Q | Hd
-  double loss = 0.0;
+  // the unit's objective partial per thread, in float-float (FP64 arithmetic
+  // in the tile loop would occupy the SM's FP64 pipe for ~500 cycles a tile)
+  float lossHi = 0.f, lossLo = 0.f;
 
   if (warp == 0) {
     // ---------------- operand producer ----------------
@@ -539,7 +541,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
       // factor copies, made once per iteration, are rounded to nearest.
       tmem_st16(tV, vv);                               // A over this tile's Vt
       tmem_st16(tBg, vt);
-      if (wantLoss) loss += (double)tl;
+      if (wantLoss) ff_add(lossHi, lossLo, tl);
       tmem_st_wait();
       fence_before_sync();
       __syncwarp();
@@ -640,7 +642,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     }
   }
   double unitLoss = 0.0;
-  if (wantLoss) unitLoss = block_sum(loss, red);
+  if (wantLoss) unitLoss = block_sum_ff(lossHi, lossLo, reinterpret_cast<float2*>(red));
   fence_before_sync();
   __syncthreads();
   if (s_abort) mbar_wait(&bars.done, 0u, 100000000ull);
