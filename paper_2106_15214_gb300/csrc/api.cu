@@ -885,7 +885,8 @@ nmf_ctx::GraphEntry* capture_step(nmf_ctx* c, uint64_t key, bool joint, int32_t 
   return &c->graphs.back();
 }
 
-// loss_dev != nullptr: asynchronous step; the loss goes to that device buffer.
+// loss_dev != nullptr: asynchronous step; the loss goes to that device buffer
+// (loss_dev == d_lossOut: it stays where the step leaves it).
 nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* loss_out, double* loss_dev) {
   c->copiesValid = g.copiesAfter;
   NMF_CU(cudaEventRecord(c->evIn, c->stream));
@@ -894,7 +895,8 @@ nmf_status replay(nmf_ctx* c, nmf_ctx::GraphEntry& g, bool wantLoss, double* los
   NMF_CU(cudaEventRecord(c->evOut, c->gs));
   NMF_CU(cudaStreamWaitEvent(c->stream, c->evOut, 0));
   if (loss_dev) {
-    NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
+    if (loss_dev != c->d_lossOut)
+      NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
     if (c->timer.on) NMF_CU(cudaStreamSynchronize(c->gs));
     c->timer.credit(g.sink, c->timer.on);
     return NMF_OK;
@@ -933,7 +935,8 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out, double*
   }
   NMF_TRY(enqueue_step(c, joint, iters, wantLoss, readback));
   if (loss_dev) {
-    NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
+    if (loss_dev != c->d_lossOut)
+      NMF_CU(cudaMemcpyAsync(loss_dev, c->d_lossOut, sizeof(double) * c->count, cudaMemcpyDeviceToDevice, c->stream));
     return NMF_OK;
   }
   if (!wantLoss) return NMF_OK;
@@ -1265,12 +1268,21 @@ nmf_status nmf_step_joint_host(nmf_ctx* c, const void* V_host, void* W_host, voi
   c->W = c->stageW; c->H = c->stageH;
   c->tableDirty = true;
   c->copiesValid = false;          // W, H come from the host
-  nmf_status s = step(c, true, iters, loss_out);
-  if (s == NMF_OK || s == NMF_ENONFINITE) {
-    nmf_status s2 = cu(cudaMemcpyAsync(W_host, c->stageW, es * c->elemsW, cudaMemcpyDeviceToHost, c->stream));
-    if (s2 == NMF_OK) s2 = cu(cudaMemcpyAsync(H_host, c->stageH, es * c->elemsH, cudaMemcpyDeviceToHost, c->stream));
-    if (s2 == NMF_OK) s2 = cu(cudaStreamSynchronize(c->stream));
-    if (s == NMF_OK) s = s2;
+  // the step, then the loss and status readback and the W, H copies back,
+  // all enqueued before one synchronisation
+  nmf_status s = step(c, true, iters, nullptr, loss_out ? c->d_lossOut : nullptr);
+  if (s == NMF_OK) s = enqueue_readback(c, loss_out != nullptr);
+  if (s == NMF_OK) s = cu(cudaMemcpyAsync(W_host, c->stageW, es * c->elemsW, cudaMemcpyDeviceToHost, c->stream));
+  if (s == NMF_OK) s = cu(cudaMemcpyAsync(H_host, c->stageH, es * c->elemsH, cudaMemcpyDeviceToHost, c->stream));
+  if (s == NMF_OK) s = cu(cudaStreamSynchronize(c->stream));
+  if (s == NMF_OK) {
+    s = complete_readback(c, loss_out != nullptr, loss_out);
+    if (s == NMF_ENONFINITE) {   // W, H were restored on the device: copy those back instead
+      nmf_status s2 = cu(cudaMemcpyAsync(W_host, c->stageW, es * c->elemsW, cudaMemcpyDeviceToHost, c->stream));
+      if (s2 == NMF_OK) s2 = cu(cudaMemcpyAsync(H_host, c->stageH, es * c->elemsH, cudaMemcpyDeviceToHost, c->stream));
+      if (s2 == NMF_OK) s2 = cu(cudaStreamSynchronize(c->stream));
+      if (s2 != NMF_OK) s = s2;
+    }
   }
   c->V = keepV; c->W = keepW; c->H = keepH; c->ldv = keepLd;
   c->tableDirty = true;

@@ -284,3 +284,47 @@ def test_floor_defaults_and_errors(lib):
     m.step_joint(3)
     Wo, Ho, _ = oracle_run(V, W0, H0, 1.0, iters=3)
     assert_close(Wd.cpu().numpy(), Wo, 1e-12, "W (default floor, FP64)")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("shape", [(90, 130, 6), (361, 2429, 49)])
+def test_host_buffer_step_matches_device_step(lib, prec, shape):
+    """nmf_step_joint_host (host V, W, H copied in, W, H and the objective
+    copied out, one synchronisation) gives the device step's iterates and
+    objectives bitwise, call after call (graph replay from the third)."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=31)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Vh = torch.tensor(V, dtype=dt).pin_memory()
+    Wh = torch.tensor(W0, dtype=dt).pin_memory()
+    Hh = torch.tensor(H0, dtype=dt).pin_memory()
+    mh = NMF(F, N, K, 1.5, precision=prec)
+    lh = [mh.step_joint_host(Vh, Wh, Hh, 1) for _ in range(4)]
+    md = NMF(F, N, K, 1.5, precision=prec)
+    Vd, Wd, Hd = to_dev(V, prec), to_dev(W0, prec), to_dev(H0, prec)
+    md.set_dense(Vd)
+    ld = []
+    for _ in range(4):
+        md.set_factors(Wd, Hd)          # each host step starts from W, H copied in
+        ld.append(md.step_joint(1))
+    assert lh == ld
+    assert torch.equal(Wh, Wd.cpu()) and torch.equal(Hh, Hd.cpu())
+
+
+def test_host_buffer_step_nonfinite_restores_the_factors(lib):
+    """A NaN in host V: NMF_ENONFINITE, and the host W, H come back as they went in."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF, NMFError
+    V, W0, H0 = problem(60, 80, 4, seed=32)
+    V[3, 5] = np.nan
+    Vh = torch.tensor(V, dtype=torch.float32).pin_memory()
+    Wh = torch.tensor(W0, dtype=torch.float32).pin_memory()
+    Hh = torch.tensor(H0, dtype=torch.float32).pin_memory()
+    m = NMF(60, 80, 4, 1.0, precision="fp32")
+    with pytest.raises(NMFError) as e:
+        m.step_joint_host(Vh, Wh, Hh, 1)
+    assert e.value.code == 4
+    assert torch.equal(Wh, torch.tensor(W0, dtype=torch.float32))
+    assert torch.equal(Hh, torch.tensor(H0, dtype=torch.float32))
