@@ -16,19 +16,23 @@
 //                already in the 128B-swizzled K-major layout the MMAs read.
 //   warp 1       V producer: the V tile of each tile step into its own ring
 //                (TMA when V's rows are 16-byte aligned, else cp.async).
-//   warp 2       MMA issuer (converged warp, an elected lane issues): MMA1
-//                of tile t into one of 4 TMEM Vt buffers as soon as its
-//                operands are in, MMA2/MMA3 of a tile as soon as its A/B
-//                tiles are, so the tensor core and the CUDA cores overlap.
-//                Every A operand is read from TMEM (the MMA1 tile, moved
-//                there once, and the epilogue's A/B tiles): about 2.5x the
-//                issue rate of shared-memory A operands, and no shared-memory
-//                traffic for them.
+//   warp 2       MMA issuer (converged warp, an elected lane issues, the
+//                warp sleeping in each wait): MMA1 of a batch of 4 tiles
+//                into one of 2 TMEM Vt buffers, MMA2/MMA3 of a tile as soon
+//                as its A/B tiles are written, so the tensor core and the
+//                CUDA cores overlap. Every A operand is read from TMEM (the
+//                MMA1 tile, moved there once, and the epilogue's A/B tiles):
+//                about 2.5x the issue rate of shared-memory A operands, and
+//                no shared-memory traffic for them.
+//   warp 3       side jobs: column norms and the objective's final sum from
+//                the previous kernel's partials.
 //   warps 4-19   epilogue: Vt from TMEM and V from shared memory to
 //                registers, the powers (and the objective), A and B back to
 //                TMEM. Two groups of 8 warps take alternate tiles; each
 //                thread owns one TMEM lane and 16 of the tile's 32 streamed
 //                indices.
+// Before the dependency wait on the previous kernel: TMEM allocation, barrier
+// initialisation, the tensor maps' prefetch and the first V tiles.
 // mbarriers connect the roles; every wait is bounded (1 s) and a timeout sets
 // NMF_ETIMEOUT, makes every role leave its loop, and frees the TMEM.
 //
