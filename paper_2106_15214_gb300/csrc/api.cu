@@ -637,6 +637,10 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     // partials; the next sweep's idle warps reduce them (and the objective of
     // the first sweep), or (H first) the normalisation kernel does.
     const bool sideScheme = tci == 2 && joint && L == 1 && fuse && norm;
+    // the second sweep reads W~, H~ and V before the epilogue ahead of it
+    // has finished (NMF_TC_EARLY=0: it waits for it at entry)
+    const char* earlyEnv = std::getenv("NMF_TC_EARLY");
+    const int early = (earlyEnv && earlyEnv[0] == '0') ? 0 : SWEEP_EARLY;
     if (sideScheme) {
       SideJob sj;
       const int nparts = rows_epilogue_grid(pl.totW, rows_epilogue_lanes(pl, tci));
@@ -651,7 +655,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         if constexpr (std::is_same<T, float>::value) sj.norms = c->hpf[0].norms;
         NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
         NMF_TRY(rows_epi(SEL_TILDE, 1, FUSE_NORM_PART | FUSE_NO_FINALIZE));
-        NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C, &sj));
+        NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C | early, &sj));
         if (fuseCopies) {
           if constexpr (std::is_same<T, float>::value)
             NMF_CU(timed(&c->timer, st, "cols_epilogue", 1,
@@ -663,7 +667,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
       } else {
         NMF_TRY(col_sweep(SEL_TILDE, SEL_TILDE, OP_SELF, CL));
         NMF_TRY(cols_epi(SEL_TILDE, 1, 0));
-        NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C, lossHere ? &sj : nullptr));
+        NMF_TRY(row_sweep(SEL_TILDE, SEL_TILDE, OP_CHI, C | early, lossHere ? &sj : nullptr));
         NMF_TRY(rows_epi(SEL_TILDE, 0, FUSE_NORM_PART | FUSE_NO_FINALIZE));
         NMF_CU(timed(&c->timer, st, "normalize", 1, [&] {
           return launch_normalize_parts<T>(pl, reinterpret_cast<const T*>(c->d_normPart), nparts, status, st);

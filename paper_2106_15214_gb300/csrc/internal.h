@@ -117,7 +117,13 @@ inline cudaError_t ensure_smem_attr(const void* func, size_t bytes) {
 // Operand selectors of the sweeps (see sweeps_impl.cuh).
 enum { SEL_CUR = 0, SEL_TILDE = 1 };      // W or Wt, H or Ht
 enum { OP_SELF = 0, OP_CHI = 1 };         // D1 = D2 = Hp (C1 = C2 = Wp) or the chi buffers
-enum { SWEEP_CONTRACT = 1, SWEEP_LOSS = 2 };
+// SWEEP_EARLY (warp-specialised sweeps, the second sweep of a joint
+// iteration): the MMA1 operands (W~, H~ copies) and V do not depend on the
+// previous kernel, so only the MMA2/3 operand loads, the side jobs and the
+// write-out wait for it. Safe because the kernel before such a sweep (an
+// epilogue) signals its dependents only after its own dependency wait: when
+// the sweep starts, everything two kernels back has completed.
+enum { SWEEP_CONTRACT = 1, SWEEP_LOSS = 2, SWEEP_EARLY = 4 };
 enum { EPI_UPDATE = 0, EPI_GRAD = 1 };
 
 // Device tables of a context for element type T.

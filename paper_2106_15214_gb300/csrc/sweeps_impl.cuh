@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(NTH)
 rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
                      int* __restrict__ status, int tc, EpiFuse fz, int G) {
-  pdl_trigger();
   pdl_wait();
+  pdl_trigger();                 // after the wait: see SWEEP_EARLY
   // With fusion every block must reach the completion counter, so a set status
   // word only skips the arithmetic.
   const bool skip = *status != 0;
@@ -443,8 +443,8 @@ __global__ void __launch_bounds__(EW)
 cols_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                      int mode, int basesel, int want_chi, BetaParams bp, T* __restrict__ gout,
                      int* __restrict__ status, int tc, EpiFuse fz, int totH) {
-  pdl_trigger();
   pdl_wait();
+  pdl_trigger();                 // after the wait: see SWEEP_EARLY
   const bool skip = *status != 0;
   if (skip && !(fz.flags & FUSE_LOSS)) return;
   const int b = blockIdx.x;
@@ -508,8 +508,8 @@ template <int BK>
 __global__ void __launch_bounds__(EW)
 cols_epilogue_vec4_kernel(const Prob<float>* __restrict__ probs, int basesel, int want_chi, BetaParams bp,
                           int* __restrict__ status, int tc, EpiFuse fz, int totQ) {
-  pdl_trigger();
   pdl_wait();
+  pdl_trigger();                 // after the wait: see SWEEP_EARLY
   const bool skip = *status != 0;
   if (skip && !(fz.flags & FUSE_LOSS)) return;
   const int b = blockIdx.x;

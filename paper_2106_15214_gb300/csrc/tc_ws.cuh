@@ -269,6 +269,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
   // padding blocks of the last cluster (s0 >= sLim) stream nothing and add zeros
   const int ntilesGeom = ws_tiles(P, ROW, geo);
   const bool wantLoss = flags & SWEEP_LOSS;
+  const bool early = flags & SWEEP_EARLY;
   const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
   const uint32_t dBytes = (uint32_t)kp * 128u;
   const uint32_t opTx = dBytes * (CHI ? 2u : 1u);
@@ -311,6 +312,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
           __syncwarp();
         }
         if (t >= nop && !__all_sync(0xffffffffu, role_wait(&bars.opempty[st], ph ^ 1u, &s_abort, status))) break;
+        if (early && t == 0) pdl_wait();              // the MMA2/3 operands come from the previous kernel
         unsigned char* sb = base + L.op0 + st * L.op_bytes;
         if (elect_one()) {
           mbar_arrive_expect_tx(&bars.opfull[st], opTx);
@@ -450,7 +452,8 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     if (elect_one()) mma_commit(&bars.done);
     __syncwarp();
   } else if (warp == 3) {
-    // ---------------- side job (persistent step kernel) ----------------
+    // ---------------- side job ----------------
+    if (early && side) pdl_wait();                  // it reads the previous kernels' partials
     side_run(side, lane, K);
   } else if (warp >= EPI_WARP0) {
     // ---------------- epilogue ----------------
@@ -559,6 +562,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
   }
 
   // ---------------- accumulators: cluster tree, then one partial slice ----------------
+  if (early) pdl_wait();                              // (long since satisfied: the producer waited)
   // Epilogue thread (mrow, grp) owns kp / 2 consecutive columns of [P | Q] in
   // TMEM lane mrow: groups 0-1 the first accumulator, 2-3 the second.
   const bool epi = warp >= EPI_WARP0;
@@ -718,8 +722,10 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CU
   if (warp == 1 && vPre > 0)
     ws_v_issue<ROW>(tmV, P, geo, vPre, base + ws_layout((P.K + 15) & ~15, CHI, nop, nv).v0, bars);
   // from here on the previous kernel's writes (the factor copies, the status
-  // word) are visible; the status is read once for the whole block
-  pdl_wait();
+  // word) are visible; the status is read once for the whole block. Early
+  // sweeps read it without waiting (a status the previous kernel sets stops
+  // the kernels after this one) and wait where they need its data.
+  if (!(flags & SWEEP_EARLY)) pdl_wait();
   if (threadIdx.x == 0) s_skip = *status != 0;
   __syncthreads();
   const bool skip = s_skip != 0;    // the block still runs to the end (cluster barriers)
@@ -785,7 +791,7 @@ tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   fence_after_sync();
   if (warp == 1 && vPre > 0)
     ws_v_issue<false>(tmV, P, geo0, vPre, base + ws_layout((P.K + 15) & ~15, CHI, nop, nv).v0, bars);
-  pdl_wait();
+  if (!(flags & SWEEP_EARLY)) pdl_wait();               // as in tc_ws_kernel
   if (threadIdx.x == 0) s_skip = *status != 0;
   __syncthreads();
   const bool skip = s_skip != 0;
@@ -794,7 +800,10 @@ tc_ws_sk_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   sj.normStride = gridDim.x;
   sj.nloss = blockIdx.x == 0 ? side.nloss : 0;
   const SideJob* sp = (sj.normK >= 0 || sj.nloss > 0) ? &sj : nullptr;
-  if (a >= b && warp == 3) side_run(sp, threadIdx.x & 31, P.K);   // no unit: run it directly
+  if (a >= b && warp == 3) {                       // no unit: run the side job directly
+    if (flags & SWEEP_EARLY) pdl_wait();
+    side_run(sp, threadIdx.x & 31, P.K);
+  }
   double l = 0.0;
   bool first = true;
   for (int64_t st = a; st < b;) {

@@ -303,3 +303,25 @@ def test_fused_copies_are_dropped_by_set_factors_and_other_calls(lib):
     f.step_joint(2)
     torch.cuda.synchronize()
     assert torch.equal(Wd, W2) and torch.equal(Hd, H2)
+
+
+@pytest.mark.parametrize("F,N,K,order", [(361, 2429, 49, "W"), (513, 20000, 20, "W"), (513, 20000, 20, "H"),
+                                         (200, 300, 20, "H")])
+def test_early_second_sweep_matches_waiting_one(lib, monkeypatch, F, N, K, order):
+    """The second sweep of a joint iteration reads W~, H~ and V before the
+    epilogue ahead of it has finished; bitwise the same iterates and
+    objectives as with the sweep waiting for it at entry (NMF_TC_EARLY=0)."""
+    from paper_2106_15214_gb300.binding import NMF
+    V, W0, H0 = problem(F, N, K, seed=41)
+    out = []
+    for early in ("1", "0"):
+        monkeypatch.setenv("NMF_TC_EARLY", early)
+        m = NMF(F, N, K, 0.5, precision="tf32", order=order)
+        Vd, Wd, Hd = dev(V), dev(W0), dev(H0)
+        m.set_dense(Vd)
+        m.set_factors(Wd, Hd)
+        losses = [m.step_joint(1) for _ in range(4)] + [m.step_joint(3)]
+        out.append((Wd.cpu().numpy(), Hd.cpu().numpy(), losses))
+    (Wa, Ha, la), (Wb, Hb, lb) = out
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+    assert la == lb
