@@ -109,7 +109,20 @@ nmf_status nmf_set_options(nmf_ctx* ctx, nmf_precision precision, nmf_order orde
  * method. NaN or Inf: NMF_EINVAL. */
 nmf_status nmf_set_floor(nmf_ctx* ctx, double eps);
 
-/* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
+/* Tile-shape autotuner for the SIMT sweeps (NMF_FP64, NMF_FP32 and batched
+ * contexts, whose work items are (problem, chunk of 32-wide tiles)): times
+ * `trials` >= 1 joint steps for each cap in {8, 16, 32, 64, 128} on the number
+ * of tiles one block sums (more chunks: more, shorter blocks and more partial
+ * slices) and keeps the fastest. W, H and the status word are restored after
+ * every trial, so the call leaves the factors as it found them. Choices are
+ * cached per process under a shape signature (count, sums of F and N, largest
+ * K, beta, precision, SM count); a cached signature returns at once. The cap
+ * changes the order of the partial sums, so iterates differ from the default
+ * tiling by rounding only. *chunk_cap (nullable) receives the choice; sparse
+ * and single-problem tensor-core contexts: NMF_EUNSUPPORTED. Synchronises. */
+nmf_status nmf_autotune(nmf_ctx* ctx, int32_t trials, int32_t* chunk_cap);
+
+/* Number L >= 1 of inner passes/* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
  * Algorithm 1) per outer iteration. */
 nmf_status nmf_set_subiterations(nmf_ctx* ctx, int32_t L);
 

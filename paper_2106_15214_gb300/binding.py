@@ -19,7 +19,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 ORDERS = {"W": W_FIRST, "H": H_FIRST, "auto": ORDER_AUTO}
 
 EXPORTS = [
-    "nmf_create", "nmf_batch_create", "nmf_set_options", "nmf_set_floor", "nmf_set_subiterations", "nmf_set_dense",
+    "nmf_create", "nmf_batch_create", "nmf_set_options", "nmf_set_floor", "nmf_autotune",
+    "nmf_set_subiterations", "nmf_set_dense",
     "nmf_set_csr", "nmf_set_factors", "nmf_batch_set_packed", "nmf_step_joint",
     "nmf_step_alternating", "nmf_loss", "nmf_grad", "nmf_kkt", "nmf_batch_get_losses",
     "nmf_get_status", "nmf_step_joint_host", "nmf_set_timing", "nmf_get_timing", "nmf_reset_timing",
@@ -49,6 +50,7 @@ def _declare(lib):
                              ctypes.POINTER(P)],
         "nmf_set_options": [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, ctypes.c_int, P],
         "nmf_set_floor": [P, D],
+        "nmf_autotune": [P, I32, ctypes.POINTER(I32)],
         "nmf_set_subiterations": [P, I32],
         "nmf_set_dense": [P, P, I64],
         "nmf_set_csr": [P, I64, P, P, P],
@@ -153,6 +155,12 @@ class NMF:
         if floor is not None:
             self.set_floor(floor)
         self._keep = []
+
+    def autotune(self, trials=3):
+        """nmf_autotune (FP64 / FP32 contexts): returns the chosen chunk cap."""
+        cap = ctypes.c_int32(0)
+        check(self._lib.nmf_autotune(self._ctx, int(trials), ctypes.byref(cap)), "nmf_autotune")
+        return cap.value
 
     def set_floor(self, eps):
         """Clamp every update to eps (nmf_set_floor); eps < 0 restores the default."""
@@ -278,6 +286,12 @@ class BatchedNMF:
         check(lib.nmf_set_options(self._ctx, self.precision, self.order, int(normalize), 0.0, 1, s),
               "nmf_set_options")
 
+    def autotune(self, trials=3):
+        """nmf_autotune: time each chunk cap over `trials` steps, keep the fastest; returns it."""
+        cap = ctypes.c_int32(0)
+        check(self._lib.nmf_autotune(self._ctx, int(trials), ctypes.byref(cap)), "nmf_autotune")
+        return cap.value
+
     def set_packed(self, Vp, Wp, Hp):
         self._keep = (Vp, Wp, Hp)
         check(self._lib.nmf_batch_set_packed(self._ctx, _ptr(Vp), _ptr(Wp), _ptr(Hp)), "nmf_batch_set_packed")
@@ -309,3 +323,52 @@ class BatchedNMF:
             self.close()
         except Exception:
             pass
+
+
+_beta_divergence_fn = None
+
+
+def _beta_divergence_function():
+    """The torch.autograd.Function, made on first use (torch is imported lazily)."""
+    global _beta_divergence_fn
+    if _beta_divergence_fn is not None:
+        return _beta_divergence_fn
+    import torch
+
+    class BetaDivergence(torch.autograd.Function):
+        """D_beta(V + kappa | WH + kappa) (eq. obj_fct, eq. beta-div) with the
+        gradient of nmf_grad: grad_W = [(WH)^(beta-2) . (WH - V)] H^T and
+        grad_H = W^T [(WH)^(beta-2) . (WH - V)], the difference of the MU
+        ratio's denominator and numerator (Sec. 4.1.5), from one pass of the
+        library's kernels with the product recomputed per tile. V is not
+        differentiated."""
+
+        @staticmethod
+        def forward(ctx, V, W, H, beta, kappa):
+            F, K = W.shape
+            N = H.shape[1]
+            prec = "fp64" if W.dtype == torch.float64 else "fp32"
+            m = NMF(F, N, K, float(beta), precision=prec, normalize=False, kappa=float(kappa))
+            Vc, Wc, Hc = V.detach().contiguous(), W.detach().contiguous(), H.detach().contiguous()
+            m.set_dense(Vc)
+            m.set_factors(Wc, Hc)
+            gW, gH = torch.empty_like(Wc), torch.empty_like(Hc)
+            loss = m.grad(gW, gH, want_loss=True)     # one pass: the objective and both gradients
+            m.close()
+            ctx.save_for_backward(gW, gH)
+            return torch.tensor(loss, dtype=W.dtype, device=W.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gW, gH = ctx.saved_tensors
+            return None, g * gW, g * gH, None, None
+
+    _beta_divergence_fn = BetaDivergence
+    return BetaDivergence
+
+
+def beta_divergence(V, W, H, beta, kappa=0.0):
+    """Differentiable D_beta(V + kappa | WH + kappa) of CUDA tensors V (F x N),
+    W (F x K), H (K x N), float32 or float64; backward gives grad_W, grad_H
+    (nmf_grad). Returns a 0-d tensor on W's device."""
+    return _beta_divergence_function().apply(V, W, H, beta, kappa)

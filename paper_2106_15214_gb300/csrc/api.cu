@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -98,6 +100,7 @@ struct nmf_ctx {
   cudaStream_t gs = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr;
   int sms = 148;
+  int chunkCap = 64;               // SIMT sweeps: most 64- or 32-wide tiles per chunk (nmf_autotune)
 };
 
 namespace {
@@ -150,21 +153,22 @@ struct Tiling {
 };
 
 // Splits of the two sweeps: enough blocks to fill the GPU twice over for a
-// single problem; for batches, chunks capped so no block walks a whole long
-// row or column of a big member while small members finish early.
-Tiling tiling(int64_t F, int64_t N, int sms, bool batched) {
+// single problem; for batches, chunks capped (at `cap` tiles, 64 unless
+// nmf_autotune chose another) so no block walks a whole long row or column of
+// a big member while small members finish early.
+Tiling tiling(int64_t F, int64_t N, int sms, bool batched, int cap) {
   Tiling t;
   t.rowTilesF = (int)cdiv(F, BF);
   t.colTilesN = (int)cdiv(N, BN);
   const int64_t nTiles = cdiv(N, BN), fTiles = cdiv(F, BF);
   const int64_t target = 2LL * sms;
   int64_t S = batched ? 1 : std::max<int64_t>(1, cdiv(target, t.rowTilesF));
-  S = std::max<int64_t>(S, cdiv(nTiles, 64));
+  S = std::max<int64_t>(S, cdiv(nTiles, cap));
   S = std::min<int64_t>(S, nTiles);
   t.chunkN = cdiv(nTiles, S) * BN;
   t.S = (int)cdiv(N, t.chunkN);
   int64_t R = batched ? 1 : std::max<int64_t>(1, cdiv(target, t.colTilesN));
-  R = std::max<int64_t>(R, cdiv(fTiles, 64));
+  R = std::max<int64_t>(R, cdiv(fTiles, cap));
   R = std::min<int64_t>(R, fTiles);
   t.chunkF = cdiv(fTiles, R) * BF;
   t.R = (int)cdiv(F, t.chunkF);
@@ -277,7 +281,7 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     const int64_t F = c->F[i], N = c->N[i];
     const int K = c->K[i];
     maxK = std::max(maxK, K);
-    tl[i] = tiling(F, N, c->sms, c->batched);
+    tl[i] = tiling(F, N, c->sms, c->batched, c->chunkCap);
     probs[i].F = F; probs[i].N = N; probs[i].K = K;
     probs[i].tcS = probs[i].tcR = 1;
     probs[i].tcSplitS = probs[i].tcSplitR = 1;
@@ -1233,6 +1237,87 @@ nmf_status nmf_batch_get_losses(nmf_ctx* c, double* out_host) {
   if (!c || !out_host) return NMF_EINVAL;
   if (!c->lossValid) return NMF_ENOTREADY;
   std::copy(c->lastLosses.begin(), c->lastLosses.end(), out_host);
+  return NMF_OK;
+}
+
+// Tile-shape autotuner for the SIMT sweeps (FP64, FP32 and batched contexts):
+// every candidate chunk cap is timed over `trials` joint steps from the same
+// W, H (restored after each), and the fastest is kept. Choices are cached per
+// process under a shape signature, so a second context of the same shape
+// skips the timing.
+namespace {
+std::mutex g_tuneMu;
+std::map<std::vector<int64_t>, int> g_tuneCache;
+}  // namespace
+
+nmf_status nmf_autotune(nmf_ctx* c, int32_t trials, int32_t* chunk_cap) {
+  if (!c || trials < 1) return NMF_EINVAL;
+  if (c->sparse || (!c->batched && (c->prec == NMF_TF32 || c->prec == NMF_BF16))) return NMF_EUNSUPPORTED;
+  if (!data_ready(c)) return NMF_ENOTREADY;
+  std::vector<int64_t> sig = {c->count, (int64_t)c->prec, (int64_t)std::llround(c->beta * 1e6), c->batched ? 1 : 0};
+  int64_t sf = 0, sn = 0, mk = 0;
+  for (int i = 0; i < c->count; ++i) { sf += c->F[i]; sn += c->N[i]; mk = std::max<int64_t>(mk, c->K[i]); }
+  sig.push_back(sf); sig.push_back(sn); sig.push_back(mk); sig.push_back(c->sms);
+  {
+    std::lock_guard<std::mutex> lk(g_tuneMu);
+    auto it = g_tuneCache.find(sig);
+    if (it != g_tuneCache.end()) {
+      if (c->chunkCap != it->second) { c->chunkCap = it->second; c->prepared = false; }
+      if (chunk_cap) *chunk_cap = it->second;
+      return NMF_OK;
+    }
+  }
+  const size_t es = esize(c);
+  void* W = c->batched ? c->Wp : c->W;
+  void* H = c->batched ? c->Hp : c->H;
+  void *bW = nullptr, *bH = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  nmf_status s = NMF_OK;
+  if (cudaMalloc(&bW, es * c->elemsW) != cudaSuccess || cudaMalloc(&bH, es * c->elemsH) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    s = NMF_ENOMEM;
+  }
+  if (s == NMF_OK) s = cu(cudaMemcpyAsync(bW, W, es * c->elemsW, cudaMemcpyDeviceToDevice, c->stream));
+  if (s == NMF_OK) s = cu(cudaMemcpyAsync(bH, H, es * c->elemsH, cudaMemcpyDeviceToDevice, c->stream));
+  const int caps[] = {8, 16, 32, 64, 128};
+  const int keep = c->chunkCap;
+  int best = keep;
+  float bestMs = 3.4e38f;
+  auto restore = [&]() -> nmf_status {
+    NMF_CU(cudaMemcpyAsync(W, bW, es * c->elemsW, cudaMemcpyDeviceToDevice, c->stream));
+    NMF_CU(cudaMemcpyAsync(H, bH, es * c->elemsH, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->d_status) NMF_CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return NMF_OK;
+  };
+  for (int cap : caps) {
+    if (s != NMF_OK) break;
+    c->chunkCap = cap;
+    c->prepared = false;                          // the next step rebuilds the plan with this cap
+    s = step(c, true, 1, nullptr);                // warm-up (and the plan)
+    if (s == NMF_OK) s = restore();
+    if (s == NMF_OK) s = cu(cudaEventRecord(e0, c->stream));
+    if (s == NMF_OK) s = step(c, true, trials, nullptr);
+    if (s == NMF_OK) s = cu(cudaEventRecord(e1, c->stream));
+    if (s == NMF_OK) s = cu(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    if (s == NMF_OK) s = cu(cudaEventElapsedTime(&ms, e0, e1));
+    if (s == NMF_OK && ms < bestMs) { bestMs = ms; best = cap; }
+    if (s == NMF_OK) s = restore();
+  }
+  if (s == NMF_OK) s = cu(cudaStreamSynchronize(c->stream));
+  c->chunkCap = s == NMF_OK ? best : keep;
+  c->prepared = false;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (bW) cudaFree(bW);
+  if (bH) cudaFree(bH);
+  if (s != NMF_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_tuneMu);
+    g_tuneCache[sig] = best;
+  }
+  if (chunk_cap) *chunk_cap = best;
   return NMF_OK;
 }
 

@@ -328,3 +328,34 @@ def test_host_buffer_step_nonfinite_restores_the_factors(lib):
     assert e.value.code == 4
     assert torch.equal(Wh, torch.tensor(W0, dtype=torch.float32))
     assert torch.equal(Hh, torch.tensor(H0, dtype=torch.float32))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1.5, 2.0, 3.0])
+def test_autograd_beta_divergence(lib, prec, beta):
+    """binding.beta_divergence (a torch.autograd.Function over nmf_grad): the
+    value is D_beta, backward scales the library's one-pass gradient by the
+    incoming gradient, matching the oracle's gradient and central finite
+    differences of the forward value."""
+    import torch
+    from paper_2106_15214_gb300.binding import beta_divergence
+    V, W0, H0 = problem(40, 55, 4, seed=51)
+    Vd = to_dev(V, prec)
+    W = to_dev(W0, prec).requires_grad_()
+    H = to_dev(H0, prec).requires_grad_()
+    D = beta_divergence(Vd, W, H, beta)
+    (2.5 * D).backward()
+    rtol = 1e-10 if prec == "fp64" else 2e-4
+    assert D.item() == pytest.approx(O.D_beta(V, W0 @ H0, beta), rel=1e-12 if prec == "fp64" else 1e-5)
+    gWo, gHo = O.gradients(V, W0, H0, beta)
+    for got, want in ((W.grad, gWo), (H.grad, gHo)):
+        got = got.double().cpu().numpy()
+        assert np.allclose(got, 2.5 * want, rtol=rtol, atol=rtol * np.abs(want).max() * 2.5)
+    if prec == "fp64":
+        h = 1e-6
+        for (i, j) in ((0, 0), (7, 2), (39, 3)):
+            Wp, Wm = W.detach().clone(), W.detach().clone()
+            Wp[i, j] += h
+            Wm[i, j] -= h
+            fd = (beta_divergence(Vd, Wp, H.detach(), beta).item() - beta_divergence(Vd, Wm, H.detach(), beta).item()) / (2 * h)
+            assert fd * 2.5 == pytest.approx(W.grad[i, j].item(), rel=1e-6, abs=1e-8)

@@ -162,3 +162,53 @@ def test_malformed_csr_is_rejected_before_use(lib):
     with pytest.raises(NMFError) as ei:
         m.step_joint(1)
     assert ei.value.code == NMF_EINVAL
+
+
+def test_batched_autotune(lib):
+    """nmf_autotune on a batched context: picks one of the candidate chunk
+    caps, leaves the packed factors exactly as it found them, a second context
+    of the same shapes gets the cached choice, and the tuned context still
+    matches the oracle."""
+    import torch
+    from paper_2106_15214_gb300.binding import BatchedNMF
+    probs = inputs.batched_hyperspectral(count=40, F_range=(20, 200), N_range=(50, 3000), K_range=(2, 24), seed=13)
+    shapes = [p.shape for p in probs]
+    Vp, Wp, Hp = pack(probs)
+    b = BatchedNMF(shapes, 1.5)
+    Vd, Wd, Hd = dev(Vp), dev(Wp), dev(Hp)
+    b.set_packed(Vd, Wd, Hd)
+    W0d, H0d = Wd.clone(), Hd.clone()
+    cap = b.autotune(trials=2)
+    assert cap in (8, 16, 32, 64, 128)
+    torch.cuda.synchronize()
+    assert torch.equal(Wd, W0d) and torch.equal(Hd, H0d)
+    b2 = BatchedNMF(shapes, 1.5)
+    b2.set_packed(dev(Vp), dev(Wp), dev(Hp))
+    assert b2.autotune(trials=2) == cap
+    b.step_joint(2)
+    per = b.losses()
+    Ws = unpack(Wd.double().cpu().numpy(), shapes, "W")
+    Hs = unpack(Hd.double().cpu().numpy(), shapes, "H")
+    for i in (0, 7, 19, 39):
+        p = probs[i]
+        Wo, Ho, lo = O.run(p.V, p.W0, p.H0, 1.5, iters=2)
+        assert rel(Ws[i], Wo) < 2e-4, i
+        assert rel(Hs[i], Ho) < 2e-4, i
+        assert per[i] == pytest.approx(lo[1], rel=1e-5)
+
+
+def test_single_problem_autotune_fp64(lib):
+    """The autotuner on a single FP64 problem keeps FP64 parity (1e-12)."""
+    from paper_2106_15214_gb300.binding import NMF
+    p = inputs.dense_kl_small()
+    F, N, K = p.shape
+    m = NMF(F, N, K, 1.0, precision="fp64")
+    import torch
+    V, W, H = dev(p.V, torch.float64), dev(p.W0, torch.float64), dev(p.H0, torch.float64)
+    m.set_dense(V)
+    m.set_factors(W, H)
+    assert m.autotune(trials=2) in (8, 16, 32, 64, 128)
+    m.step_joint(3)
+    Wo, Ho, _ = O.run(p.V, p.W0, p.H0, 1.0, iters=3)
+    assert rel(W.cpu().numpy(), Wo) < 1e-12
+    assert rel(H.cpu().numpy(), Ho) < 1e-12
