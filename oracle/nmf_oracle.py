@@ -13,7 +13,7 @@ equation states.
 
 Shapes: V is F x N, W is F x K, H is K x N (Sec. 2.1, eq. nmf).
 
-Readings of points the paper leaves open (each is listed again in the design doc):
+Readings of points the paper leaves open:
   * 0 log 0 = 0 in the KL divergence (beta = 1), so d_1(0 | y) = y.
   * kappa (Sec. 4.1.3 "Handling zero values") is added to V and to every
     product WH that enters an update or the objective; default 0.

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (derivations in DESIGN.md, "Tolerances"):
+Tolerances:
   FP64: 1e-12 relative on W, H after one iteration; 1e-8 relative on the
         objective after 200 iterations (small dense KL case).
   FP32: every sum here has nonnegative terms, so recursive summation of n

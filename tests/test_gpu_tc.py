@@ -1,6 +1,6 @@
 """Tensor-core (tcgen05 kind::tf32) path against the FP64 oracle.
 
-TF32 tolerance (derivation in DESIGN.md, "Tolerances"): every operand of the
+TF32 tolerance: every operand of the
 three products is rounded to a 10-bit mantissa (u = 2^-11); each product term
 then errs by at most ~2u relative and sums of nonnegative terms keep that
 bound, the elementwise powers scale the error of Vt by |beta - 2|, and the MU
