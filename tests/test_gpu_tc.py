@@ -1,11 +1,12 @@
 """Tensor-core (tcgen05 kind::tf32) path against the FP64 oracle.
 
-TF32 tolerance: every operand of the
-three products is rounded to a 10-bit mantissa (u = 2^-11); each product term
-then errs by at most ~2u relative and sums of nonnegative terms keep that
-bound, the elementwise powers scale the error of Vt by |beta - 2|, and the MU
-ratio, gamma and chi compound a few such factors: 1e-2 relative on W, H after
-one iteration bounds it; the objective at the iterate is within 2e-3.
+TF32 tolerance: the factor operands of the three products are rounded to a
+10-bit mantissa (u = 2^-11) and the A/B tiles truncated to it by the tensor
+core (< 2u); each product term then errs by at most ~2u-3u relative and sums
+of nonnegative terms keep that bound, the elementwise powers scale the error
+of Vt by |beta - 2|, and the MU ratio, gamma and chi compound a few such
+factors: 1e-2 relative on W, H after one iteration bounds it; the objective
+at the iterate is within 2e-3.
 """
 import numpy as np
 import pytest
