@@ -54,7 +54,7 @@ typedef enum {
   NMF_ECUDA = 3,         /* a CUDA runtime call failed */
   NMF_ENONFINITE = 4,    /* an update produced Inf/NaN; W, H restored */
   NMF_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-  NMF_EUNSUPPORTED = 6,  /* valid request this build does not implement */
+  NMF_EUNSUPPORTED = 6,  /* valid request the library does not implement */
   NMF_ENOTREADY = 7      /* data or factors not set yet */
 } nmf_status;
 

@@ -1432,7 +1432,7 @@ const char* nmf_status_string(nmf_status s) {
     case NMF_ECUDA: return "NMF_ECUDA: CUDA runtime error";
     case NMF_ENONFINITE: return "NMF_ENONFINITE: non-finite value in an update";
     case NMF_ETIMEOUT: return "NMF_ETIMEOUT: device wait timed out";
-    case NMF_EUNSUPPORTED: return "NMF_EUNSUPPORTED: not supported by this build";
+    case NMF_EUNSUPPORTED: return "NMF_EUNSUPPORTED: not supported by this library";
     case NMF_ENOTREADY: return "NMF_ENOTREADY: data or factors not set";
   }
   return "unknown nmf_status";
