@@ -63,8 +63,9 @@ __device__ __forceinline__ T phase_a(const T* Ws, int KP, const T* Hs, int K,
   return tl;
 }
 
+// float: three blocks per SM (80 registers, no spills; 128 at two blocks)
 template <typename T, int BK, int KJ>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
 row_sweep_kernel(const Prob<T>* __restrict__ probs, int count, const int* __restrict__ prefix,
                  int wsel, int hsel, int dsel, int flags, BetaParams bp,
                  double* __restrict__ lossPart, const int* __restrict__ status) {
