@@ -32,6 +32,9 @@ L2_FLUSH_BYTES = 512 << 20
 WORKLOADS = {
     "faces": dict(gen="dense_quadratic_faces", beta=2.0, desc="dense quadratic (beta=2) faces F=361 N=2429 K=49"),
     "spectrogram": dict(gen="dense_is_spectrogram", beta=0.0, desc="dense Itakura-Saito (beta=0) F=513 N=20000 K=20"),
+    # V = 410 MB, well above the 129 MB L2: every sweep streams V from HBM
+    "spectrogram_large": dict(gen="dense_is_spectrogram", kw={"N": 200000}, beta=0.0,
+                              desc="dense Itakura-Saito (beta=0) F=513 N=200000 K=20"),
     "kl_small": dict(gen="dense_kl_small", beta=1.0, desc="dense KL (beta=1) F=200 N=500 K=10"),
 }
 
@@ -74,7 +77,7 @@ def parse():
 def problem(name):
     from paper_2106_15214_gb300 import inputs
     wl = WORKLOADS[name]
-    return getattr(inputs, wl["gen"])(), wl
+    return getattr(inputs, wl["gen"])(**wl.get("kw", {})), wl
 
 
 def cpu_threads():

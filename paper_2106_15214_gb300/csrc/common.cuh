@@ -216,12 +216,15 @@ __device__ __forceinline__ float dbeta_stable(float x, float y, float beta, int 
   float phi;
   if (fabsf(u) < 0.1f) {
     phi = series_phi(u, c);
-  } else if (bk == BK_KL) {
-    phi = (1.0f + u) * log1pf(u) - u;
-  } else if (bk == BK_IS) {
-    phi = u - log1pf(u);
   } else {
-    phi = (expm1f(beta * log1pf(u)) - beta * u) / (beta * (beta - 1.0f));
+    // log(x / y): log1p of u where x - y is exact (y / 2 <= x <= 2 y), else the
+    // log of the ratio itself; u = x / y - 1 rounds to -1 once x / y < 2^-24
+    // and log1p(u) would turn into -inf
+    const float r = x / y;
+    const float lr = (r >= 0.5f && r <= 2.0f) ? log1pf(u) : logf(r);
+    if (bk == BK_KL) phi = r * lr - u;
+    else if (bk == BK_IS) phi = u - lr;
+    else phi = (expm1f(beta * lr) - beta * u) / (beta * (beta - 1.0f));
   }
   float yb = (bk == BK_KL) ? y : (bk == BK_IS ? 1.0f : powf(y, beta));
   return yb * phi;
@@ -265,11 +268,13 @@ __device__ __forceinline__ float dbeta_fast(float x, float y, float beta, const 
   constexpr float LN2 = 0.69314718056f;
   if (BK == BK_EUC) { const float d = x - y; return 0.5f * d * d; }
   if (BK == BK_KL && x <= 0.0f) return y;
-  const float u = (x - y) * rcp_fast(y);
+  // the logarithm of the ratio itself: 1 + (x - y) / y rounds to 0 once x / y
+  // < 2^-24, which would make the term infinite
+  const float r = x * rcp_fast(y), u = r - 1.0f, lr = LN2 * lg2_fast(r);
   float phi;
-  if (BK == BK_KL) phi = (1.0f + u) * (LN2 * lg2_fast(1.0f + u)) - u;
-  else if (BK == BK_IS) phi = u - LN2 * lg2_fast(1.0f + u);
-  else phi = (ex2_fast(beta * lg2_fast(1.0f + u)) - 1.0f - beta * u) * rcp_fast(beta * (beta - 1.0f));
+  if (BK == BK_KL) phi = r * lr - u;
+  else if (BK == BK_IS) phi = u - lr;
+  else phi = (ex2_fast(beta * lg2_fast(r)) - 1.0f - beta * u) * rcp_fast(beta * (beta - 1.0f));
   const float yb = (BK == BK_KL) ? y : (BK == BK_IS ? 1.0f : ex2_fast(beta * lg2_fast(y)));
   return yb * phi;
 }

@@ -326,3 +326,15 @@ def test_early_second_sweep_matches_waiting_one(lib, monkeypatch, F, N, K, order
     (Wa, Ha, la), (Wb, Hb, lb) = out
     assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
     assert la == lb
+
+
+def test_tf32_spectrogram_large_matches_oracle(lib):
+    """513 x 200000 (V = 410 MB, above L2): one JMM iteration with W first
+    through the stream-K column sweep (about 175 tile steps per block) and the
+    fused copies; every entry of W and H against the FP64 oracle."""
+    p = inputs.dense_is_spectrogram(N=200000)
+    W, H, loss, _ = run_tc(p.V, p.W0, p.H0, 0.0, "jmm", 1, "W")
+    Wo, Ho, lo = O.run(p.V, p.W0, p.H0, 0.0, iters=1)
+    assert maxrel(W, Wo) < TF32_RTOL
+    assert maxrel(H, Ho) < TF32_RTOL
+    assert loss == pytest.approx(lo[0], rel=TF32_LOSS_RTOL)
