@@ -259,7 +259,7 @@ __device__ __forceinline__ void ab_terms_fast(float v, float vt, float bm2, floa
 // The objective's terms for the tensor-core path, branch-free, with the
 // approximations above (natural log = lg2 * ln 2). There Vt carries TF32
 // rounding (relative ~1e-3), so each term is already uncertain by about
-// |u| 1e-3 with u = (x - y) / y; the direct forms' cancellation error near
+// |u| 1e-3 with u = x / y - 1; the direct forms' cancellation error near
 // u = 0 (about 2e-7 absolute) is far below that, and the small-|u| series of
 // dbeta_stable would only make warps diverge.
 template <int BK>
