@@ -59,6 +59,18 @@ def test_host_validation(built):
         assert built.nmf_step_joint(ctx, 1, ctypes.byref(loss)) == 7       # no data yet
         assert built.nmf_step_joint(ctx, 0, None) == 1
         assert built.nmf_set_csr(ctx, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16)) == 1  # beta != 1
+        built.nmf_set_floor.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        assert built.nmf_set_floor(ctx, float("nan")) == 1
+        assert built.nmf_set_floor(ctx, float("inf")) == 1
+        assert built.nmf_set_floor(ctx, 1e-20) == 0
+        assert built.nmf_set_floor(ctx, -1.0) == 0                      # back to the default
+        assert built.nmf_set_floor(None, 0.0) == 1
+        cap = ctypes.c_int32(0)
+        assert built.nmf_autotune(ctx, 0, ctypes.byref(cap)) == 1          # trials < 1
+        assert built.nmf_autotune(ctx, 2, ctypes.byref(cap)) == 7          # no data yet
+        assert built.nmf_autotune(None, 2, None) == 1
+        assert built.nmf_set_options(ctx, 2, 0, 1, 0.0, 1, None) == 0      # TF32 single problem
+        assert built.nmf_autotune(ctx, 2, ctypes.byref(cap)) == 6          # the tensor-core path has its own model
     finally:
         built.nmf_destroy(ctx)
     built.nmf_destroy(None)
