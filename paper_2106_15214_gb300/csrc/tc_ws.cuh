@@ -382,8 +382,8 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     //   j - 1, MMA1 of batch j (its buffer's previous batch, j - 2, has been
     //   issued completely one tile earlier, so its completion is near).
     // A sleeping warp takes no issue slots from the epilogue warps that share
-    // its scheduler, and wakes when the barrier completes; a polling loop
-    // over several queues measured one tile-period of reaction time.
+    // its scheduler and wakes when the barrier completes (a loop polling the
+    // queues in turn measured the same step time; the fixed order is simpler).
     // Every A operand is read from TMEM, every B operand from shared memory.
     // Descriptors are built once; an operand at byte offset o is the base
     // descriptor plus o / 16 (the start-address field, bits 0-13, cannot carry
