@@ -1,0 +1,52 @@
+"""bench.py on the CPU: the reference arm's JSON line (the oracle timed on the
+host cores) and the host-side helpers the GPU arm relies on."""
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "iters/s" and d["higher_is_better"] is True
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["vs_baseline"] is None and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert "faces" in d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_algorithmic_bytes():
+    F, N, K, s = 361, 2429, 49, 4
+    V, FK, KN = F * N * s, F * K * s, K * N * s
+    assert bench.algorithmic_bytes("tc_row_sweep", F, N, K) == V + FK + 3 * KN + 2 * FK
+    assert bench.algorithmic_bytes("tc_col_sweep", F, N, K) == V + 3 * FK + KN + 2 * KN
+    assert bench.algorithmic_bytes("cols_epilogue", F, N, K) == 7 * KN + 5 * FK
+    assert bench.algorithmic_bytes("nope", F, N, K) is None
+
+
+def test_clock_sampler_keeps_samples_inside_the_timed_region():
+    c = bench.ClockSampler(0)
+    t = time.monotonic()
+    fields = "0, {sm}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {cap}"
+    c.lines = [(t - 1.0, fields.format(sm=600, hw="Not Active", cap="Not Active")),        # before: ignored
+               (t + 0.01, fields.format(sm=2070, hw="Not Active", cap="Active")),
+               (t + 0.02, fields.format(sm=2055, hw="Not Active", cap="Not Active")),
+               (t + 5.0, fields.format(sm=300, hw="Active", cap="Not Active"))]           # after: ignored
+    c.window = (t, t + 0.03)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_max_mhz"] == 2070.0
+    assert s["sm_mhz"] == (2070 + 2055) / 2
+    assert s["reasons"] == ["sw_power_cap"]
