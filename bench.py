@@ -199,14 +199,22 @@ def barrier(world):
         dist.barrier()
 
 
-def reduce_max(x, world):
+def reduce_max(x, world, device="cuda"):
+    """Max of a host scalar over the ranks (the NCCL group's device, or "cpu"
+    under a gloo group)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world, steps, max_seconds):
+    """Whole-job throughput: every rank runs `steps` steps of its own replica;
+    the job takes the slowest rank's time."""
+    return world * steps / max_seconds
 
 
 def algorithmic_bytes(kernel, F, N, K, esize=4):
@@ -377,7 +385,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
     dev_s_max = reduce_max(dev_s, world)
-    value = world * args.steps / dev_s_max
+    value = aggregate_rate(world, args.steps, dev_s_max)
     losses = loss_dev[:args.steps].cpu().tolist()
     # Kernel pass: the same steps with the library's per-kernel CUDA events on
     # the launching stream (they add a little time per launch, so the value

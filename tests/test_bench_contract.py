@@ -50,3 +50,42 @@ def test_clock_sampler_keeps_samples_inside_the_timed_region():
     assert s["samples"] == 2 and s["sm_max_mhz"] == 2070.0
     assert s["sm_mhz"] == (2070 + 2055) / 2
     assert s["reasons"] == ["sw_power_cap"]
+
+
+def _two_rank_worker(rank, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    try:
+        bench.barrier(2)
+        m = bench.reduce_max(1.5 + rank, 2, device="cpu")
+        rate = bench.aggregate_rate(2, 100, m)
+        with open(os.path.join(out_dir, f"r{rank}"), "w") as f:
+            f.write(f"{m} {rate}")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_helpers_on_two_gloo_ranks(tmp_path):
+    """The N > 1 helpers (barrier, max over ranks, whole-job rate) on two CPU
+    ranks: both see the slower rank's time and the same aggregate."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.spawn(_two_rank_worker, args=(port, str(tmp_path)), nprocs=2, join=True)
+    for r in (0, 1):
+        m, rate = map(float, open(tmp_path / f"r{r}").read().split())
+        assert m == 2.5 and rate == 2 * 100 / 2.5
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as two ranks, only rank 0 runs the oracle and prints its line."""
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+                          "--master-addr", "127.0.0.1", "--master-port", "0", os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and json.loads(lines[0])["impl"] == "reference"
