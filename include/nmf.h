@@ -122,7 +122,7 @@ nmf_status nmf_set_floor(nmf_ctx* ctx, double eps);
  * and single-problem tensor-core contexts: NMF_EUNSUPPORTED. Synchronises. */
 nmf_status nmf_autotune(nmf_ctx* ctx, int32_t trials, int32_t* chunk_cap);
 
-/* Number L >= 1 of inner passes/* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
+/* Number L >= 1 of inner passes of Algorithm 2 (and L_W = L_H = L of
  * Algorithm 1) per outer iteration. */
 nmf_status nmf_set_subiterations(nmf_ctx* ctx, int32_t L);
 

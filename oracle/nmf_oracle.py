@@ -29,7 +29,9 @@ Readings of points the paper leaves open:
     (the default) is the unconstrained method.
 
 Parity status of each function is stated in its docstring; every function here
-is pinned by tests/test_oracle_pins.py unless it says "parity unpinned".
+is pinned by tests/test_oracle_pins.py (the gamma = 1 heuristic and BMM with
+L_W, L_H > 1 by tests/test_oracle_variants.py) unless it says "parity
+unpinned".
 """
 from __future__ import annotations
 
