@@ -225,6 +225,19 @@ nmf_status nmf_get_timing(nmf_ctx* ctx, int32_t i, const char** name, int64_t* l
 /* Clears the timing records and launch counts. */
 nmf_status nmf_reset_timing(nmf_ctx* ctx);
 
+/* Test support for failure detection (the paper has no counterpart). Every
+ * device-side wait of the library's persistent kernels gives up after a
+ * bounded time, sets the status word to NMF_ETIMEOUT and lets the kernel run
+ * to its end without further work; the next synchronising call then returns
+ * NMF_ETIMEOUT. This call sets that bound for the grid barriers of the
+ * persistent kernels to limit_ns (1e6 .. 1e10 ns; default 1e9) and makes
+ * those barriers expect extra_arrivals (0 or 1) arrivals beyond the launched
+ * blocks, so that with 1 every such wait runs out (a flag nothing sets): a
+ * test can exercise the timeout path without a fault or a hang. Other values
+ * -> NMF_EINVAL. Call with (1000000000, 0) to restore the defaults. A status
+ * word left at NMF_ETIMEOUT is cleared by nmf_set_factors. */
+nmf_status nmf_set_barrier_test(nmf_ctx* ctx, int64_t limit_ns, int32_t extra_arrivals);
+
 /* Objective without any device allocation. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code
  * running while a CUDA stream capture is active, hosts that give the library a
@@ -234,8 +247,10 @@ nmf_status nmf_reset_timing(nmf_ctx* ctx);
  * FP64, without a context.
  *
  * Arguments: sizes, beta, kappa and precision as for nmf_create and
- * nmf_set_options (NMF_FP64 means double buffers, every other precision
- * float). V_dev (F x N, leading dimension ldv >= N), W_dev (F x K) and H_dev
+ * nmf_set_options; precision only selects the element type: NMF_FP64 means
+ * double buffers and FP64 arithmetic, every other precision float buffers
+ * and the FP32 evaluation that nmf_loss also uses for NMF_TF32 and NMF_BF16
+ * contexts. V_dev (F x N, leading dimension ldv >= N), W_dev (F x K) and H_dev
  * (K x N) are caller-owned device inputs, row-major; loss_dev is a
  * caller-owned device double that receives the result. The call is
  * asynchronous on cuda_stream (NULL: legacy default stream): read *loss_dev
@@ -247,9 +262,10 @@ nmf_status nmf_reset_timing(nmf_ctx* ctx);
  * Limit: ceil(F/32) * ceil(N/32) <= 65536 (for example 8192 x 8192), else
  * NMF_EINVAL and nothing is launched. All calls share the array; calls whose
  * kernels overlap on the GPU (other streams, other host threads) race on it,
- * so serialise them. The first call on each device looks up the array's
- * device address (once per device, with that device current); make that
- * first call before any stream capture begins. */
+ * so serialise them. Every call looks up the array's device address in the
+ * current device's context (an allocation-free query, so a device reset is
+ * harmless); the first call on a device also loads the library's device code
+ * there, so make that first call before any stream capture begins. */
 nmf_status nmf_loss_noalloc(int64_t F, int64_t N, int32_t K, double beta, double kappa,
                             nmf_precision precision, const void* V_dev, int64_t ldv,
                             const void* W_dev, const void* H_dev, double* loss_dev,

@@ -24,7 +24,7 @@ EXPORTS = [
     "nmf_set_csr", "nmf_set_factors", "nmf_batch_set_packed", "nmf_step_joint",
     "nmf_step_alternating", "nmf_loss", "nmf_grad", "nmf_kkt", "nmf_batch_get_losses",
     "nmf_get_status", "nmf_step_joint_host", "nmf_set_timing", "nmf_get_timing", "nmf_reset_timing",
-    "nmf_loss_noalloc", "nmf_step_joint_async", "nmf_step_alternating_async", "nmf_destroy", "nmf_status_string",
+    "nmf_loss_noalloc", "nmf_set_barrier_test", "nmf_step_joint_async", "nmf_step_alternating_async", "nmf_destroy", "nmf_status_string",
 ]
 
 _lib = None
@@ -70,6 +70,7 @@ def _declare(lib):
         "nmf_get_timing": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(I64), PD],
         "nmf_reset_timing": [P],
         "nmf_loss_noalloc": [I64, I64, I32, D, D, ctypes.c_int, P, I64, P, P, P, P],
+        "nmf_set_barrier_test": [P, I64, I32],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -122,8 +123,23 @@ def loss_noalloc(V, W, H, beta, kappa=0.0, out=None, stream=None):
     Asynchronous on the stream; returns `out`."""
     import torch
     lib = load()
+    for t, nm in ((V, "V"), (W, "W"), (H, "H")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2):
+            raise TypeError(f"{nm} must be a 2-D CUDA tensor")
+        if t.dtype not in (torch.float64, torch.float32) or t.dtype != V.dtype:
+            raise TypeError(f"V, W and H must share one dtype, float64 or float32 (got {nm}: {t.dtype})")
+        if t.device != V.device:
+            raise ValueError("V, W and H must be on one device")
     F, N = V.shape
     K = W.shape[1]
+    if V.stride(1) != 1 or V.stride(0) < N:
+        raise ValueError("V must be row-major with unit column stride")
+    if tuple(W.shape) != (F, K) or tuple(H.shape) != (K, N):
+        raise ValueError(f"W must be {F} x K and H K x {N}")
+    if not (W.is_contiguous() and H.is_contiguous()):
+        raise ValueError("W and H must be contiguous")
+    if out is not None and not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise TypeError("out must be a float64 CUDA tensor")
     prec = FP64 if V.dtype == torch.float64 else FP32
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=V.device)
@@ -149,7 +165,7 @@ class NMF:
         self._ctx = ctypes.c_void_p()
         check(lib.nmf_create(self.F, self.N, self.K, self.beta, ctypes.byref(self._ctx)), "nmf_create")
         self._stream = stream
-        self.set_options()
+        self.set_options(stream)
         if L != 1:
             check(lib.nmf_set_subiterations(self._ctx, int(L)), "nmf_set_subiterations")
         if floor is not None:
@@ -326,6 +342,24 @@ class BatchedNMF:
 
 
 _beta_divergence_fn = None
+_grad_contexts = {}
+
+
+def _grad_context(F, N, K, beta, kappa, dtype, device):
+    """A context per (shape, beta, kappa, dtype, device, stream), kept for reuse
+    by the autograd function (contexts own device scratch: creating one per
+    call would allocate every time)."""
+    import torch
+    prec = "fp64" if dtype == torch.float64 else "fp32"
+    stream = torch.cuda.current_stream(device).cuda_stream
+    key = (F, N, K, float(beta), float(kappa), prec, device.index, stream)
+    m = _grad_contexts.get(key)
+    if m is None:
+        if len(_grad_contexts) >= 16:
+            _grad_contexts.pop(next(iter(_grad_contexts))).close()
+        m = NMF(F, N, K, float(beta), precision=prec, normalize=False, kappa=float(kappa), stream=stream)
+        _grad_contexts[key] = m
+    return m
 
 
 def _beta_divergence_function():
@@ -339,28 +373,38 @@ def _beta_divergence_function():
         """D_beta(V + kappa | WH + kappa) (eq. obj_fct, eq. beta-div) with the
         gradient of nmf_grad: grad_W = [(WH)^(beta-2) . (WH - V)] H^T and
         grad_H = W^T [(WH)^(beta-2) . (WH - V)], the difference of the MU
-        ratio's denominator and numerator (Sec. 4.1.5), from one pass of the
-        library's kernels with the product recomputed per tile. V is not
-        differentiated."""
+        ratio's denominator and numerator (Sec. 4.1.5). Forward evaluates the
+        objective only (stream-ordered, into device memory, when the problem
+        fits nmf_loss_noalloc's scratch); backward runs one nmf_grad pass
+        over the saved tensors, recomputing the product tile by tile. V is not
+        differentiated. Contexts are cached per shape and reused."""
 
         @staticmethod
         def forward(ctx, V, W, H, beta, kappa):
             F, K = W.shape
             N = H.shape[1]
-            prec = "fp64" if W.dtype == torch.float64 else "fp32"
-            m = NMF(F, N, K, float(beta), precision=prec, normalize=False, kappa=float(kappa))
             Vc, Wc, Hc = V.detach().contiguous(), W.detach().contiguous(), H.detach().contiguous()
-            m.set_dense(Vc)
-            m.set_factors(Wc, Hc)
-            gW, gH = torch.empty_like(Wc), torch.empty_like(Hc)
-            loss = m.grad(gW, gH, want_loss=True)     # one pass: the objective and both gradients
-            m.close()
-            ctx.save_for_backward(gW, gH)
-            return torch.tensor(loss, dtype=W.dtype, device=W.device)
+            if ((F + 31) // 32) * ((N + 31) // 32) <= 65536:
+                loss = loss_noalloc(Vc, Wc, Hc, beta, kappa)[0].to(W.dtype)
+            else:
+                m = _grad_context(F, N, K, beta, kappa, W.dtype, W.device)
+                m.set_dense(Vc)
+                m.set_factors(Wc, Hc)
+                loss = torch.tensor(m.loss(), dtype=W.dtype, device=W.device)
+            ctx.save_for_backward(Vc, Wc, Hc)
+            ctx.beta, ctx.kappa = float(beta), float(kappa)
+            return loss
 
         @staticmethod
         def backward(ctx, g):
-            gW, gH = ctx.saved_tensors
+            Vc, Wc, Hc = ctx.saved_tensors
+            F, K = Wc.shape
+            N = Hc.shape[1]
+            m = _grad_context(F, N, K, ctx.beta, ctx.kappa, Wc.dtype, Wc.device)
+            m.set_dense(Vc)
+            m.set_factors(Wc, Hc)
+            gW, gH = torch.empty_like(Wc), torch.empty_like(Hc)
+            m.grad(gW, gH)                 # asynchronous: no host round trip
             return None, g * gW, g * gH, None, None
 
     _beta_divergence_fn = BetaDivergence

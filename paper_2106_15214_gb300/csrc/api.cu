@@ -101,6 +101,10 @@ struct nmf_ctx {
   cudaEvent_t evIn = nullptr, evOut = nullptr;
   int sms = 148;
   int chunkCap = 64;               // SIMT sweeps: most 64- or 32-wide tiles per chunk (nmf_autotune)
+  // nmf_set_barrier_test: bound of the persistent kernels' barrier waits and
+  // arrivals they expect beyond the launched blocks
+  uint64_t waitLimitNs = 1000000000ull;
+  unsigned extraArrivals = 0;
 };
 
 namespace {
@@ -616,6 +620,11 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         a.normPart = reinterpret_cast<float*>(c->d_normPart);
         a.gridBar = c->d_counter + 16;
         a.status = status;
+        a.extraArrivals = c->extraArrivals;
+        a.waitLimitNs = c->waitLimitNs;
+        // both barrier words start at zero: a launch whose barrier wait timed
+        // out leaves its arrivals count behind
+        NMF_CU(cudaMemsetAsync(a.gridBar, 0, 2 * sizeof(unsigned), st));
         NMF_CU(timed(&c->timer, st, "tc_step", 1,
                      [&] { return launch_tc_step(c->hpf[0], c->tcmaps, bp, a, c->sms, st); }));
       }
@@ -1050,6 +1059,15 @@ nmf_status nmf_set_floor(nmf_ctx* c, double eps) {
   if (!c || std::isnan(eps) || std::isinf(eps)) return NMF_EINVAL;
   invalidate_graphs(c);
   c->floorEps = eps < 0.0 ? -1.0 : eps;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_barrier_test(nmf_ctx* c, int64_t limit_ns, int32_t extra_arrivals) {
+  if (!c || limit_ns < 1000000 || limit_ns > 10000000000LL || extra_arrivals < 0 || extra_arrivals > 1)
+    return NMF_EINVAL;
+  invalidate_graphs(c);
+  c->waitLimitNs = (uint64_t)limit_ns;
+  c->extraArrivals = (unsigned)extra_arrivals;
   return NMF_OK;
 }
 

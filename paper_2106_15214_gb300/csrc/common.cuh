@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace nmf {
 
 // Compile-time specialisation of beta. The paper singles out beta = 0, 1, 2
@@ -38,16 +40,29 @@ struct BetaParams {
   double floor = 0.0;  // every update is clamped to >= floor (0: off)
   int kind;
   float series[7];  // Taylor coefficients of phi_beta(u) for u^2 .. u^8 (fill_series)
+  float tiny = 0.f; // small-Vt guard threshold of the single-precision kernels (fill_series)
 };
 
 // phi_b(u) = ((1+u)^b - 1 - b u) / (b (b-1)) = sum_{j>=2} c_j u^j with
 // c_2 = 1/2 and c_{j+1} = c_j (b - j) / (j + 1); computed once on the host.
+//
+// Also the small-Vt guard threshold (not in the paper; the precision pattern
+// asks for it): in single precision the power Vt^(beta-2) overflows once
+// Vt < FLT_MAX^(-1/(2-beta)) (beta < 2), and the hardware reciprocal,
+// logarithm and reciprocal square root flush subnormal Vt to zero, although
+// A = V Vt^(beta-2) and B = Vt^(beta-1) may still be representable. Entries
+// with Vt below 2^max(-125, -120/(2-beta)) (beta < 2; 2^-125 for beta > 2;
+// no guard at beta = 2, where A = V and B = Vt) take their powers and their
+// objective term in FP64 instead. At beta = 0 this is Vt < 2^-60.
 inline void fill_series(BetaParams& bp) {
   double c = 0.5;
   for (int j = 2; j <= 8; ++j) {
     bp.series[j - 2] = (float)c;
     c *= (bp.beta - (double)j) / (double)(j + 1);
   }
+  double e = -125.0;
+  if (bp.beta < 2.0) e = -120.0 / (2.0 - bp.beta) > e ? -120.0 / (2.0 - bp.beta) : e;
+  bp.tiny = bp.beta == 2.0 ? 0.f : (float)std::ldexp(1.0, (int)std::floor(e));
 }
 
 // One problem of a (possibly batched) context. Every pointer is device memory.
@@ -156,6 +171,25 @@ __device__ __forceinline__ void ab_terms(T v, T vt, T bm2, T& A, T& B) {
     T p = pow_t(vt, bm2);
     A = v * p;
     B = vt * p;
+  }
+}
+
+// ab_terms with the small-Vt guard (fill_series): float entries whose
+// product lies below bp.tiny take their powers in FP64 (rare; a warp-uniform
+// branch in the common case). Double is unguarded.
+template <int BK>
+__device__ __forceinline__ void ab_terms_g(double v, double vt, double bm2, double& A, double& B, float) {
+  ab_terms<BK, double>(v, vt, bm2, A, B);
+}
+template <int BK>
+__device__ __forceinline__ void ab_terms_g(float v, float vt, float bm2, float& A, float& B, float tiny) {
+  if (vt < tiny) {
+    double a, b;
+    ab_terms<BK, double>((double)v, (double)vt, (double)bm2, a, b);
+    A = (float)a;
+    B = (float)b;
+  } else {
+    ab_terms<BK, float>(v, vt, bm2, A, B);
   }
 }
 
@@ -279,12 +313,31 @@ __device__ __forceinline__ float dbeta_fast(float x, float y, float beta, const 
   return yb * phi;
 }
 
+// The tensor-core epilogue's terms of one entry (v, y = Vt, both with kappa):
+// A, B and, with the objective, d_beta(v | y) added to tl; the small-Vt guard
+// takes entries below bp.tiny to FP64 (powers and objective term).
+template <int BK>
+__device__ __forceinline__ void epi_terms(float v, float y, float bm2, const BetaParams& bp, bool wantLoss,
+                                          float& tl, float& A, float& B) {
+  if (y < bp.tiny) {
+    double a, b;
+    ab_terms<BK, double>((double)v, (double)y, bp.beta - 2.0, a, b);
+    A = (float)a;
+    B = (float)b;
+    if (wantLoss) tl += (float)dbeta_direct((double)v, (double)y, bp.beta, BK);
+    return;
+  }
+  if (wantLoss) tl += dbeta_fast<BK>(v, y, (float)bp.beta, bp.series);
+  ab_terms_fast<BK>(v, y, bm2, A, B);
+}
+
 template <typename T> struct DB;
 template <> struct DB<double> {
   __device__ static double eval(double x, double y, const BetaParams& bp, int bk) { return dbeta_direct(x, y, bp.beta, bk); }
 };
 template <> struct DB<float> {
   __device__ static double eval(float x, float y, const BetaParams& bp, int bk) {
+    if (y < bp.tiny) return dbeta_direct((double)x, (double)y, bp.beta, bk);   // small-Vt guard
     return (double)dbeta_stable(x, y, (float)bp.beta, bk, bp.series);
   }
 };

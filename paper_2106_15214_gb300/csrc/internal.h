@@ -291,8 +291,10 @@ struct TcStepArgs {
   double* lossPart;
   double* lossOut;
   float* normPart;      // [K][blocks]
-  unsigned* gridBar;    // two words, zero between launches
+  unsigned* gridBar;    // two words, cleared by the host before every launch
   int* status;
+  unsigned extraArrivals = 0;            // nmf_set_barrier_test
+  uint64_t waitLimitNs = 1000000000ull;
 };
 bool tc_step_supported(const Prob<float>& P, const TcMaps& m, int sms);
 cudaError_t launch_tc_step(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, const TcStepArgs& a,

@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 #include "nmf.h"
@@ -29,31 +28,24 @@ constexpr int kTile = 32;                   // tile edge (rows and columns)
 constexpr int kThreads = 256;
 constexpr int64_t kPartials = 1 << 16;      // largest number of 32 x 32 tiles
 constexpr size_t kScratchBytes = sizeof(double) * kPartials + 256;
-constexpr int kMaxDevices = 64;
 
 // Partial sums at offset 0, the completion counter right after them.
 static __device__ __align__(256) unsigned char g_loss_scratch[kScratchBytes];
 
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Once per device, with that device current: the device address of the array.
-// Host code must not pass the symbol itself to a kernel (it names a host-side
-// stand-in), so the address is looked up here.
+// The device address of the array in the current device's context. Host
+// code must not pass the symbol itself to a kernel (it names a host-side
+// stand-in), so the address is looked up, with the device current, on every
+// call: after a device reset or in a new context the array may sit elsewhere,
+// and the lookup allocates nothing. The first lookup on a device loads the
+// library's device code there, which is why the first call should come before
+// any stream capture.
 nmf_status scratch_for_current_device(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return NMF_ECUDA; }
-  if (dev < 0 || dev >= kMaxDevices) return NMF_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_loss_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return NMF_ECUDA;
-    }
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_loss_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return NMF_ECUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return NMF_OK;
 }
 

@@ -54,7 +54,7 @@ __device__ __forceinline__ T phase_a(const T* Ws, int KP, const T* Hs, int K,
       for (int k = 0; k < K; ++k) vt = fma(wrow[k], Hs[k * TP + lane], vt);
       vt += kappa;
       const T v = V[gf * ldv + gn] + kappa;
-      ab_terms<BK, T>(v, vt, bm2, a, b);
+      ab_terms_g<BK>(v, vt, bm2, a, b, bp.tiny);
       if (wantLoss) tl += (T)DB<T>::eval(v, vt, bp, BK);
     }
     As[f * TP + lane] = a;

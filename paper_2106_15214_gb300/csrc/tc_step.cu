@@ -44,6 +44,8 @@ struct StepParams {
   float* normPart;                        // [K][G]
   unsigned* bar;                          // [0] arrivals, [1] generation
   int* status;
+  unsigned extra;                         // arrivals expected beyond the G blocks (0; 1 in the timeout test)
+  uint64_t limitNs;                       // bound of every barrier wait (1 s unless a test shortens it)
 };
 
 __device__ __forceinline__ bool status_set(const int* st) { return *reinterpret_cast<const volatile int*>(st) != 0; }
@@ -57,14 +59,14 @@ __device__ __forceinline__ void grid_sync(const StepParams& S) {
     volatile unsigned* gen = S.bar + 1;
     const unsigned g0 = *gen;
     __threadfence();
-    if (atomicAdd(S.bar, 1u) == (unsigned)S.G - 1) {
+    if (atomicAdd(S.bar, 1u) == (unsigned)S.G + S.extra - 1) {
       atomicExch(S.bar, 0u);
       __threadfence();
       atomicAdd(S.bar + 1, 1u);
     } else {
       const uint64_t t0 = globaltimer_ns();
       while (*gen == g0) {
-        if (globaltimer_ns() - t0 > 1000000000ull) {
+        if (globaltimer_ns() - t0 > S.limitNs) {
           atomicExch(S.status, ETIMEOUT);
           break;
         }
@@ -419,6 +421,8 @@ cudaError_t launch_tc_step(const Prob<float>& P, const TcMaps& m, const BetaPara
   S.normPart = a.normPart;
   S.bar = a.gridBar;
   S.status = a.status;
+  S.extra = a.extraArrivals;
+  S.limitNs = a.waitLimitNs;
 
   void (*kern)(const StepMaps, Prob<float>, BetaParams, StepParams) = nullptr;
   switch (bp.kind) {

@@ -187,7 +187,7 @@ tc_row_sweep_kernel(Prob<float> P, int wsel, int hsel, int dsel, int flags, Beta
           b[j] = 0.f;
           if (valid) {
             const float v = vv[j] + kappa, y = vt[4 * c + j] + kappa;
-            ab_terms<BK, float>(v, y, bm2, a[j], b[j]);
+            ab_terms_g<BK>(v, y, bm2, a[j], b[j], bp.tiny);
             if (wantLoss) tl += (float)DB<float>::eval(v, y, bp, BK);
           }
         }
@@ -354,7 +354,7 @@ tc_col_sweep_kernel(Prob<float> P, int wsel, int hsel, int csel, int flags, Beta
           if (valid) {
             const float v = reinterpret_cast<const float*>(Vs)[f * MT + ncol] + kappa;
             const float y = vt[4 * c + j] + kappa;
-            ab_terms<BK, float>(v, y, bm2, a[j], b[j]);
+            ab_terms_g<BK>(v, y, bm2, a[j], b[j], bp.tiny);
             if (wantLoss) tl += (float)DB<float>::eval(v, y, bp, BK);
           }
         }

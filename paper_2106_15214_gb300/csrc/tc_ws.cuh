@@ -470,7 +470,6 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
     const int64_t gm = m0 + mrow;
     const bool mvalid = gm < mLim;
     const int jb0 = 16 * half;
-    const float beta = (float)bp.beta;
     const uint32_t tBg = tbase + TM_B + 32u * g + lane_off + jb0;
     if (ew < 4 && ntiles > 0) {
       // warps 4-7 move the A operand of MMA1 (row mrow, kp columns) from shared memory to TMEM
@@ -526,8 +525,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
         #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float v = vv[j] + kappa, y = vt[j] + kappa;
-          if (wantLoss) tl += dbeta_fast<BK>(v, y, beta, bp.series);
-          ab_terms_fast<BK>(v, y, bm2, vv[j], vt[j]);     // A into vv, B into vt
+          epi_terms<BK>(v, y, bm2, bp, wantLoss, tl, vv[j], vt[j]);   // A into vv, B into vt
         }
       } else {
         #pragma unroll
@@ -536,8 +534,7 @@ __device__ __forceinline__ double ws_unit(const CUtensorMap& tmV, const CUtensor
           vv[j] = 0.f;
           vt[j] = 0.f;
           if (mvalid && jb0 + j < nvalid) {
-            if (wantLoss) tl += dbeta_fast<BK>(v, y, beta, bp.series);
-            ab_terms_fast<BK>(v, y, bm2, vv[j], vt[j]);
+            epi_terms<BK>(v, y, bm2, bp, wantLoss, tl, vv[j], vt[j]);
           }
         }
       }

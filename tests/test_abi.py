@@ -76,6 +76,22 @@ def test_host_validation(built):
     built.nmf_destroy(None)
 
 
+def test_barrier_test_validation(built):
+    """nmf_set_barrier_test accepts bounds of 1 ms .. 10 s and 0 or 1 extra arrivals."""
+    ctx = ctypes.c_void_p()
+    assert built.nmf_create(20, 30, 3, 1.0, ctypes.byref(ctx)) == 0
+    try:
+        assert built.nmf_set_barrier_test(ctx, 999_999, 0) == 1
+        assert built.nmf_set_barrier_test(ctx, 1_000_000, 2) == 1
+        assert built.nmf_set_barrier_test(ctx, 20_000_000_000, 0) == 1
+        assert built.nmf_set_barrier_test(ctx, 1_000_000, -1) == 1
+        assert built.nmf_set_barrier_test(ctx, 1_000_000, 1) == 0
+        assert built.nmf_set_barrier_test(ctx, 1_000_000_000, 0) == 0
+        assert built.nmf_set_barrier_test(None, 1_000_000_000, 0) == 1
+    finally:
+        built.nmf_destroy(ctx)
+
+
 def test_batch_validation(built):
     ctx = ctypes.c_void_p()
     F = (ctypes.c_int64 * 2)(4, 5)

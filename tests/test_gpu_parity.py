@@ -361,6 +361,27 @@ def test_autograd_beta_divergence(lib, prec, beta):
             assert fd * 2.5 == pytest.approx(W.grad[i, j].item(), rel=1e-6, abs=1e-8)
 
 
+def test_autograd_reuses_contexts(lib):
+    """Forward alone allocates no context (the objective goes to device memory
+    through nmf_loss_noalloc); repeated backward passes of one shape share one
+    cached context; the values stay those of the oracle."""
+    import torch
+    from paper_2106_15214_gb300 import binding
+    binding._grad_contexts.clear()
+    V, W0, H0 = problem(40, 55, 4, seed=52)
+    Vd = to_dev(V, "fp64")
+    for _ in range(3):
+        D = binding.beta_divergence(Vd, to_dev(W0, "fp64"), to_dev(H0, "fp64"), 0.5)
+    assert len(binding._grad_contexts) == 0
+    assert D.item() == pytest.approx(O.D_beta(V, W0 @ H0, 0.5), rel=1e-12)
+    gWo, _ = O.gradients(V, W0, H0, 0.5)
+    for _ in range(3):
+        W = to_dev(W0, "fp64").requires_grad_()
+        binding.beta_divergence(Vd, W, to_dev(H0, "fp64"), 0.5).backward()
+        assert np.allclose(W.grad.cpu().numpy(), gWo, rtol=1e-10, atol=1e-12 * np.abs(gWo).max())
+    assert len(binding._grad_contexts) == 1
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "fp64"])
 @pytest.mark.parametrize("beta", [0.0, 1.0, 0.5, -1.0])
 def test_objective_with_tiny_ratios(lib, prec, beta):
