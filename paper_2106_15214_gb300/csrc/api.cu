@@ -292,7 +292,14 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     probs[i].tcClusterS = probs[i].tcClusterR = 1;
     probs[i].tcSK = probs[i].tcSKBlocks = 0;
     if (!c->batched) tc_tiling(probs[i], c->sms);
-    const int Smax = std::max(tl[i].S, probs[i].tcS), Rmax = std::max(tl[i].R, probs[i].tcR);
+    probs[i].fuS = 1;
+    if constexpr (std::is_same<T, float>::value) {
+      if (!c->batched && c->prec == NMF_BF16 && K <= 32 && F <= 1024) {
+        probs[i].kp = (K + 15) & ~15;
+        probs[i].fuS = std::max(1, tc_fused_clusters(probs[i], c->sms));
+      }
+    }
+    const int Smax = std::max({tl[i].S, probs[i].tcS, probs[i].fuS}), Rmax = std::max(tl[i].R, probs[i].tcR);
     const size_t FK = (size_t)F * K, KN = (size_t)K * N;
     size_t bytes = 0;
     bytes += align256(sizeof(T) * FK) * 2;                         // chiW1, chiW2
@@ -323,7 +330,7 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     P.chiW2 = take(sizeof(T) * FK);
     P.chiH1 = take(sizeof(T) * KN);
     P.chiH2 = take(sizeof(T) * KN);
-    P.rowPart = take(sizeof(T) * FK * 2 * std::max(tl[i].S, P.tcS));
+    P.rowPart = take(sizeof(T) * FK * 2 * std::max({tl[i].S, P.tcS, P.fuS}));
     P.colPart = take(sizeof(T) * KN * 2 * std::max(tl[i].R, P.tcR));
     P.norms = take(sizeof(T) * K);
     P.Wt = static_cast<T*>(c->tildeW) + oW;
@@ -375,13 +382,14 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   pl.d_prefTc = tabs + 5 * (cnt + 1);
   pl.rowSlices[0] = probs[0].S;
   pl.rowSlices[1] = probs[0].tcS;
+  pl.rowSlices[2] = probs[0].fuS;
   pl.d_prefRow = tabs; pl.totRow = pr[cnt];
   pl.d_prefCol = tabs + (cnt + 1); pl.totCol = pc[cnt];
   pl.d_prefW = tabs + 2 * (cnt + 1); pl.totW = pw[cnt];
   pl.d_prefH = tabs + 3 * (cnt + 1); pl.totH = ph[cnt];
   pl.d_prefK = tabs + 4 * (cnt + 1); pl.totK = pk[cnt];
   size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
-  if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max(tcRowGrid, tcColGrid));
+  if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max({tcRowGrid, tcColGrid, c->sms + 8}));
   NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
   if (!c->batched) {
     // W-epilogue norm partials ([K][blocks]), or [K][SMs] for the persistent step kernel
@@ -609,7 +617,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   if constexpr (std::is_same<T, float>::value) {
     const char* stepEnv = std::getenv("NMF_TC_STEP");
     const bool stepOn = stepEnv && stepEnv[0] == '1';
-    if (tc && stepOn && joint && L == 1 && norm && fuse && c->count == 1 &&
+    if (tc && c->prec == NMF_TF32 && stepOn && joint && L == 1 && norm && fuse && c->count == 1 &&
         tc_step_supported(c->hpf[0], c->tcmaps, c->sms)) {
       for (int it = 0; it < iters; ++it) {
         TcStepArgs a;
@@ -629,6 +637,39 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
                      [&] { return launch_tc_step(c->hpf[0], c->tcmaps, bp, a, c->sms, st); }));
       }
       c->lossFused = true;
+      return NMF_OK;
+    }
+  }
+  // NMF_BF16: the fused single-read H-first iteration (tc_fused.cu): copies
+  // of W~, H~ | the fused sweep (product, A, B, objective, H update, both
+  // contractions; H written) | W update from its partial slices (column norms
+  // and the objective finalised by its last block) | normalisation.
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->prec == NMF_BF16) {
+      const Prob<float>& P0 = c->hpf[0];
+      const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
+      for (int it = 0; it < iters; ++it) {
+        const bool lossHere = wantLoss && it == iters - 1;
+        NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
+                     [&] { return launch_tc_copies<float>(P0, true, true, true, status, st); }));
+        NMF_CU(timed(&c->timer, st, "tc_fused", 1, [&] {
+          return launch_tc_fused(P0, c->tcmaps, bp, ncl, lp, status, c->waitLimitNs, c->extraArrivals, st);
+        }));
+        EpiFuse f;
+        f.flags = (lossHere ? FUSE_LOSS : 0) | (norm ? FUSE_NORM_PART : 0);
+        f.lossPart = lp;
+        f.lossBlocks = cgrid;
+        f.lossOut = c->d_lossOut;
+        f.normPart = static_cast<void*>(c->d_normPart);
+        f.counter = c->d_counter;
+        NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] {
+          return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 0, bp, nullptr, status, st, 3, f);
+        }));
+        if (norm)
+          NMF_CU(timed(&c->timer, st, "normalize", 1, [&] { return launch_normalize_apply<T>(pl, status, st); }));
+      }
+      c->lossFused = true;
+      c->copiesValid = false;
       return NMF_OK;
     }
   }
@@ -930,7 +971,10 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out, double*
   NMF_TRY(prepare(c));
   if (c->sparse) NMF_TRY(ensure_sparse(c));
   const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
-  if (!c->sparse && tc && (c->batched || c->prec == NMF_BF16 || tc_kp(c->K[0]) > TC_KPMAX))
+  if (!c->sparse && tc && (c->batched || tc_kp(c->K[0]) > TC_KPMAX)) return NMF_EUNSUPPORTED;
+  // NMF_BF16 is the fused single-read joint iteration: H first, L = 1, K <= 32, F <= 1024
+  if (!c->sparse && c->prec == NMF_BF16 &&
+      (!joint || c->L != 1 || c->order == NMF_W_FIRST || !c->tcmaps.ok || !tc_fused_supported(c->hpf[0])))
     return NMF_EUNSUPPORTED;
   const bool wantLoss = loss_out != nullptr || loss_dev != nullptr;
   const bool readback = loss_dev == nullptr;

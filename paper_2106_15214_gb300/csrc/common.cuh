@@ -100,6 +100,7 @@ struct Prob {
   int tcClusterR;
   int tcSK;          // 1: the column sweep is split stream-K (below), tcR = most slices of any column tile
   int tcSKBlocks;    // blocks of the stream-K column sweep
+  int fuS = 1;       // partial slices of the fused single-read sweep (its clusters)
   int64_t tcChunkN;  // multiple of 32
   int64_t tcChunkF;  // multiple of 32
   // TF32-rounded, zero-padded operand copies read by TMA in the tensor-core

@@ -138,7 +138,7 @@ struct Plan {
   int* d_prefH = nullptr; int totH = 0;       // EW-entry blocks over K x N
   int* d_prefK = nullptr; int totK = 0;       // one block per column of W
   int* d_prefTc = nullptr;                    // {0, tc row grid, 0, tc column grid} (single problem)
-  int rowSlices[2] = {1, 1};                  // row-sweep partial slices: SIMT, tensor core (single problem)
+  int rowSlices[3] = {1, 1, 1};               // row-sweep partial slices: SIMT, tensor core, fused sweep (single problem)
   int colVec4 = 0;                            // single problem with N % 4 == 0: 16-byte H epilogue
 };
 
@@ -169,7 +169,8 @@ struct EpiFuse {
   unsigned* counter = nullptr;  // zero between launches
 };
 
-// tc != 0: the partials come from the tensor-core sweeps (tcS / tcR slices).
+// tc != 0: the partials come from the tensor-core sweeps (tcS / tcR slices);
+// tc == 3 (W epilogue only): from the fused single-read sweep (fuS slices).
 template <typename T>
 cudaError_t launch_rows_epilogue(const Plan<T>& pl, int mode, int basesel, int want_chi,
                                  const BetaParams& bp, T* gout, int* status, cudaStream_t st,
@@ -194,7 +195,7 @@ int rows_epilogue_lanes_host(int count, int slices);
 inline int rows_epilogue_grid(int totW, int G) { return (int)(((int64_t)totW * EW * G + 1023) / 1024); }
 template <typename T>
 inline int rows_epilogue_lanes(const Plan<T>& pl, int tc) {
-  return pl.count == 1 ? rows_epilogue_lanes_host(1, pl.rowSlices[tc ? 1 : 0]) : 1;
+  return pl.count == 1 ? rows_epilogue_lanes_host(1, pl.rowSlices[tc == 3 ? 2 : (tc ? 1 : 0)]) : 1;
 }
 // Tensor-core copies (TF32 shadows) of W and/or H of one problem, and with
 // `tilde` the W~, H~ copies too (the begin of a tensor-core iteration).
@@ -313,6 +314,17 @@ cudaError_t launch_tc_ws_row(const Prob<float>& P, const TcMaps& m, int dsel, in
                              double* lossPart, int* status, cudaStream_t st, const SideJob* side);
 cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, int flags, const BetaParams& bp,
                              double* lossPart, int* status, cudaStream_t st, const SideJob* side);
+
+// Fused single-read H-first JMM iteration sweep (tc_fused.cu; bf16
+// contractions, TF32 product): K <= 32, F <= 1024. It writes H (before the
+// normalisation), one [P | Q] partial slice per cluster into rowPart (ncl
+// slices) and one objective partial per block (grid = ceil(F / 128) x ncl).
+bool tc_fused_supported(const Prob<float>& P);
+// Clusters of ceil(F / 128) blocks that can be resident at once (at most the
+// number of 128-column batches); 0 when the kernel cannot launch.
+int tc_fused_clusters(const Prob<float>& P, int sms);
+cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
+                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st);
 
 // Sparse beta = 1 path (sparse_kl.cu).
 struct SparseKL {

@@ -370,7 +370,7 @@ rows_epilogue_kernel(const Prob<T>* __restrict__ probs, int count, const int* __
   const int sub = threadIdx.x % G;
   const int64_t idx = (int64_t)(b - (count == 1 ? 0 : prefix[pi])) * epb + threadIdx.x / G;
   const bool inside = idx < FK && !skip;
-  const int slices = tc ? P.tcS : P.S;
+  const int slices = tc == 3 ? P.fuS : (tc ? P.tcS : P.S);
   T num = T(0), den = T(0);
   if (inside) {
     const T* part = P.rowPart + idx;

@@ -1,0 +1,779 @@
+// tc_fused.cu -- one read of V per JMM iteration: the H-first update of
+// eq. jnt_update (L = 1; the inverted order of Sec. 4.1.1) with the product
+// Vt = Wt Ht formed once (Algorithm 2, step "Vt <- Wt Ht"; Sec. 3.4.2,
+// Table 3), A = V . Vt^(beta-2) and B = Vt^(beta-1) evaluated once, and BOTH
+// contractions taken from on-chip copies of A and B:
+//
+//   H = Ht . ((Wt^T A) / (Wt^T B))^gamma            (reduction over f)
+//   W = Wt . ((A chi_1(H, Ht)^T) / (B chi_2(H, Ht)^T))^gamma  (reduction over n)
+//
+// Work split. A cluster of c = ceil(F / 128) blocks owns a run of 128-column
+// batches of V; block r of the cluster owns rows [128 r, 128 r + 128) (the
+// TMEM lanes of its tiles). Per batch each block
+//   1. forms Vt (128 x 128, tcgen05 kind::tf32, W~ rows in TMEM, H~^T rows in
+//      shared memory) and, tile by tile (32 columns), reads V, evaluates A, B
+//      and the objective in registers (FP32; FP64 below the small-Vt guard),
+//      writes A and B as bf16 back into the Vt columns of TMEM (the A operand
+//      of the W contraction) and, transposed, into a shared-memory copy (the A
+//      operand of the H contraction, M = 128 columns n);
+//   2. contracts that copy with W~ (bf16): its partial H numerator and
+//      denominator over its 128 rows (TMEM, lanes = columns n);
+//   3. exchanges those partials inside the cluster through distributed shared
+//      memory: every block reduces 1/c of the batch's entries of H over the
+//      c partials in a fixed order, forms them (written to global memory) and
+//      chi_1, chi_2, and pushes those chi entries (bf16) into every block's
+//      operand buffer;
+//   4. contracts its TMEM copy of A and B with chi_1, chi_2 (kind::f16) into
+//      its W numerator and denominator (TMEM, accumulated over the batches).
+// At the end every block writes its [P | Q] rows as one partial slice (one per
+// cluster); the W epilogue kernel sums the slices in fixed order. The next
+// batch's product and epilogue overlap the exchange: two TMEM batch buffers,
+// two H-accumulator slots and two chi slots alternate.
+//
+// Roles (24 warps): 0 operand loads (W~ rows once, H~^T rows per batch), 1 V
+// tiles, 2 MMA issue, 3 idle, 4-19 epilogue (two groups of 8 warps on
+// alternate tiles, each thread one TMEM lane and 16 columns of a tile), 20-23
+// the exchange (one TMEM lane quarter each). Every wait is bounded (1 s, then
+// NMF_ETIMEOUT and every role leaves its loop); the blocks of a cluster meet
+// only in bounded mbarrier waits, plus one cluster barrier at entry and one at
+// exit that every block reaches.
+//
+// Precision: the product in TF32 (10-bit mantissas, FP32 accumulation), A, B,
+// W~ and chi rounded to bf16 (8-bit mantissas) for the two contractions (FP32
+// accumulation), the powers in FP32, the objective accumulated in float-float
+// then FP64. Limits: K <= 32 (kp <= 32), F <= 1024 (c <= 8).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace nmf {
+using namespace tc;
+
+namespace {
+
+constexpr int FU_THREADS = 768;
+constexpr int FU_EPI0 = 4;           // first epilogue warp
+constexpr int FU_EX0 = 20;           // first exchange warp
+constexpr int FU_MAXV = 6;
+constexpr int FU_ETIMEOUT = 5;
+constexpr uint32_t FU_TB = 16384;    // one V tile (128 x 32 floats) or one H~^T batch (128 x 32)
+constexpr size_t FU_SMEM_LIMIT = 227 * 1024;
+// TMEM columns: batch buffers 0 and 1 (Vt of 4 tiles, then [A | B] bf16 in
+// place), H-accumulator slots (Hn at +0, Hd at +32), P, Q, W~ rows (MMA1 A).
+constexpr uint32_t FT_BUF = 0, FT_HACC = 256, FT_P = 384, FT_Q = 416, FT_W = 448, FT_COLS = 512;
+
+struct FuLayout {
+  uint32_t fa0;      // 2 H~^T batch slots (128 rows x 32 floats, SW128)
+  uint32_t v0;       // nv V tiles
+  uint32_t sa, sb;   // A^T, B^T copies: 2 K-atoms (64 rows f each) x 128 rows n x 128 B (bf16, SW128)
+  uint32_t wb;       // W~^T bf16: 2 K-atoms x kp rows x 128 B
+  uint32_t chi0;     // 2 chi slots: chi_1 then chi_2, each 2 K-atoms (64 columns n) x kp rows x 128 B
+  uint32_t chiSlot;
+  uint32_t mb;       // mailbox: 2K rows (Hn then Hd) x 128 floats
+  uint32_t total;
+  int nv;
+};
+
+__host__ __device__ inline FuLayout fu_layout(int K, int kp, int nv) {
+  FuLayout L;
+  L.fa0 = 0;
+  L.v0 = 2 * FU_TB;
+  L.sa = L.v0 + (uint32_t)nv * FU_TB;
+  L.sb = L.sa + 32768u;
+  L.wb = L.sb + 32768u;
+  L.chi0 = L.wb + 2u * (uint32_t)kp * 128u;
+  L.chiSlot = 4u * (uint32_t)kp * 128u;
+  L.mb = L.chi0 + 2u * L.chiSlot;
+  L.total = L.mb + 2u * (uint32_t)K * 512u;
+  L.nv = nv;
+  return L;
+}
+
+// Deepest V ring that fits (at least 2 tiles).
+inline int fu_pick_nv(int K, int kp) {
+  for (int nv = FU_MAXV; nv >= 2; --nv)
+    if (1024 + fu_layout(K, kp, nv).total <= FU_SMEM_LIMIT) return nv;
+  return 0;
+}
+
+struct FuBars {
+  uint64_t vfull[FU_MAXV], vempty[FU_MAXV];
+  uint64_t fafull[2], fafree[2], tfull[2], buffree[2], haccfull[2], haccfree[2], chiready[2];
+  uint64_t stashfull, stashfree, once, onceT, done;
+  // arrived on by every block of the cluster, alternating by batch parity: a
+  // block can arrive for batch j + 1 before another block's arrival for batch
+  // j has landed (that one reaches the barrier only through a third block),
+  // but its arrival for j + 2 is causally after this block's own wait for j.
+  uint64_t mailfull[2], chifull[2];
+};
+
+struct FuParams {
+  int c;             // blocks per cluster (row tiles of 128)
+  int ncl;           // clusters
+  int nbatch;        // 128-column batches of V
+  int nv;
+  double* lossPart;  // one partial per block
+  int* status;
+  uint64_t limitNs;  // bound of every wait
+  unsigned extra;    // arrivals the cluster barriers expect beyond the c blocks (0; 1 in the timeout test)
+};
+
+// Bounded local wait shared by every role (gives up when another role did).
+__device__ __forceinline__ bool fu_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
+                                        uint64_t limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > limit) {
+      *abort = 1;
+      atomicExch(status, FU_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded wait for arrivals of the cluster's blocks (acquire at cluster
+// scope: their writes before arriving are visible afterwards).
+__device__ __forceinline__ bool fu_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
+                                                uint64_t limit) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > limit) {
+      *abort = 1;
+      atomicExch(status, FU_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Byte offset of bf16 element e (0..63) of row r in a 128B-swizzled K-atom.
+__device__ __forceinline__ uint32_t sw_bf16(uint32_t r, uint32_t e) { return sw128_offset(r, 2u * e); }
+
+__device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned extra) {
+  for (int s = 0; s < nv; ++s) {
+    mbar_init(&B.vfull[s], 1u);
+    mbar_init(&B.vempty[s], 8u);           // the 8 warps of the group reading the tile
+  }
+  for (int s = 0; s < 2; ++s) {
+    mbar_init(&B.fafull[s], 1u);
+    mbar_init(&B.fafree[s], 1u);
+    mbar_init(&B.tfull[s], 1u);
+    mbar_init(&B.buffree[s], 1u);
+    mbar_init(&B.haccfull[s], 1u);
+    mbar_init(&B.haccfree[s], 4u);         // the 4 exchange warps
+    mbar_init(&B.chiready[s], 4u);
+    mbar_init(&B.mailfull[s], 4u * (uint32_t)c + extra);    // every exchange warp of every block
+    mbar_init(&B.chifull[s], 4u * (uint32_t)c + extra);
+  }
+  mbar_init(&B.stashfull, 32u);            // 4 tiles x 8 warps per batch
+  mbar_init(&B.stashfree, 1u);
+  mbar_init(&B.once, 1u);
+  mbar_init(&B.onceT, 4u);
+  mbar_init(&B.done, 1u);
+  fence_mbar_init();
+}
+
+// One launch per iteration; grid = ncl clusters x c blocks.
+template <int BK>
+__global__ void __launch_bounds__(FU_THREADS, 1)
+tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmW,
+                const __grid_constant__ CUtensorMap tmH, Prob<float> P, BetaParams bp, FuParams S) {
+  pdl_trigger();
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ FuBars bars;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int s_abort;
+  __shared__ int s_skip;
+  __shared__ double red[32];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = P.K, kp = (K + 15) & ~15;
+  const int c = S.c;
+  const int r = (int)cluster_rank();                 // row tile of this block
+  const int cl = (int)(blockIdx.x / (unsigned)c);
+  const int b0 = (int)((int64_t)cl * S.nbatch / S.ncl), b1 = (int)((int64_t)(cl + 1) * S.nbatch / S.ncl);
+  const int nb = b1 - b0;
+  const int nv = S.nv;
+  const FuLayout L = fu_layout(K, kp, nv);
+  const int64_t m0 = (int64_t)r * 128;
+  const uint64_t lim = S.limitNs;
+  const int ntiles = 4 * nb;
+  const int vPre = nv < ntiles ? nv : ntiles;
+
+  // ---- prologue: TMEM, barriers, tensor maps, the first V tiles (V is never
+  // written by the step's kernels), then the dependency wait
+  if (warp == 2) tmem_alloc(&tslot, FT_COLS);
+  if (tid == 0) {
+    s_abort = 0;
+    prefetch_tmap(&tmV);
+    prefetch_tmap(&tmW);
+    prefetch_tmap(&tmH);
+    fu_init_bars(bars, nv, c, S.extra);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 1 && elect_one()) {
+    for (int t = 0; t < vPre; ++t) {
+      mbar_arrive_expect_tx(&bars.vfull[t], FU_TB);
+      tma_load_2d(base + L.v0 + t * FU_TB, &tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[t]);
+    }
+  }
+  __syncwarp();
+  pdl_wait();
+  // W~^T (bf16, the B operand of the H contraction) from the full-precision
+  // W~; chi slots zeroed (their padded rows k >= K stay zero)
+  for (int i = tid; i < 128 * kp; i += FU_THREADS) {
+    const int k = i / 128, f = i - k * 128;
+    const float w = (k < K && m0 + f < P.F) ? P.Wt[(m0 + f) * K + k] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+    *reinterpret_cast<__nv_bfloat16*>(base + L.wb + (f >> 6) * (kp * 128) + sw_bf16(k, f & 63)) = h;
+  }
+  for (uint32_t o = tid * 16u; o < 2u * L.chiSlot; o += FU_THREADS * 16u)
+    *reinterpret_cast<uint4*>(base + L.chi0 + o) = make_uint4(0u, 0u, 0u, 0u);
+  fence_smem_to_async();
+  // every block of the cluster has its barriers and buffers ready before any
+  // block arrives on them or writes into them; block 0 of the cluster decides
+  // for all whether the status word stops this launch
+  cluster_sync();
+  if (r == 0 && tid == 0) {
+    const int sk = *S.status != 0;
+    for (int q = 0; q < c; ++q) {
+      const uint32_t a = dsmem_map((const void*)&s_skip, (uint32_t)q);
+      asm volatile("st.shared::cluster.b32 [%0], %1;" :: "r"(a), "r"(sk) : "memory");
+    }
+  }
+  cluster_sync();
+  const bool skip = s_skip != 0;
+  const int nbr = skip ? 0 : nb;                      // batches this launch runs
+  const uint32_t tbase = tslot;
+  float lossHi = 0.f, lossLo = 0.f;
+
+  if (warp == 0) {
+    // ---------------- operand loads ----------------
+    if (nbr > 0 && elect_one()) {
+      mbar_arrive_expect_tx(&bars.once, FU_TB);
+      tma_load_2d(base + L.sa, &tmW, 0, (int)m0, &bars.once);          // W~ rows (staging over the A^T copy)
+    }
+    __syncwarp();
+    int issued = 0;
+    for (int j = 0; j < nbr; ++j, ++issued) {
+      const int s = j & 1;
+      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.fafree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
+                                                       S.status, lim)))
+        break;
+      if (elect_one()) {
+        mbar_arrive_expect_tx(&bars.fafull[s], FU_TB);
+        tma_load_2d(base + L.fa0 + s * FU_TB, &tmH, 0, (int)(128 * (int64_t)(b0 + j)), &bars.fafull[s]);
+      }
+      __syncwarp();
+    }
+    // after a timeout no copy may land once the block has ended: wait (bounded)
+    // for the last loads of each slot (their consumers may have given up)
+    if (s_abort && nbr > 0) {
+      mbar_wait(&bars.once, 0u, 100000000ull);
+      for (int j = issued > 2 ? issued - 2 : 0; j < issued; ++j)
+        mbar_wait(&bars.fafull[j & 1], (uint32_t)(j >> 1) & 1u, 100000000ull);
+    }
+  } else if (warp == 1) {
+    // ---------------- V tiles ----------------
+    const int nt = 4 * nbr;
+    for (int t = nt; t < vPre; ++t)                    // issued before the skip decision: wait for them
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars.vfull[t], 0u, 100000000ull))) break;
+    int issued = nt < vPre ? nt : vPre;               // the first tiles went out before the dependency wait
+    for (int t = vPre; t < nt; ++t, ++issued) {
+      const int sv = t % nv;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.vempty[sv], (uint32_t)((t / nv) - 1) & 1u, &s_abort, S.status, lim)))
+        break;
+      if (elect_one()) {
+        mbar_arrive_expect_tx(&bars.vfull[sv], FU_TB);
+        tma_load_2d(base + L.v0 + sv * FU_TB, &tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[sv]);
+      }
+      __syncwarp();
+    }
+    if (s_abort)                                       // as above: the last tile of every slot
+      for (int t = issued > nv ? issued - nv : 0; t < issued; ++t)
+        mbar_wait(&bars.vfull[t % nv], (uint32_t)(t / nv) & 1u, 100000000ull);
+  } else if (warp == 2) {
+    // ---------------- MMA issue ----------------
+    // MMA1(j): Vt of batch j into buffer j & 1. H-MMA(j): the A^T, B^T copies
+    // times W~ into H-accumulator slot j & 1. W-MMA(j): [A | B] of buffer
+    // j & 1 times chi slot j & 1 into P, Q. Order: MMA1(0), MMA1(1), then per
+    // j: H-MMA(j) (as soon as the epilogue has finished batch j, so that the
+    // exchange of batch j starts at once), W-MMA(j - 1), MMA1(j + 1) (its
+    // buffer is the one W-MMA(j - 1) read); finally W-MMA(last). The exchange
+    // of batch j thus runs while the epilogue works on batch j + 1.
+    const uint32_t id1 = idesc(128, 128, kFmtTF32), idk = idesc(128, kp, kFmtBF16);
+    const uint64_t dFa = desc_sw128(smem_u32(base + L.fa0));
+    const uint64_t dSA = desc_sw128(smem_u32(base + L.sa)), dSB = desc_sw128(smem_u32(base + L.sb));
+    const uint64_t dWb = desc_sw128(smem_u32(base + L.wb)), dChi = desc_sw128(smem_u32(base + L.chi0));
+    const uint32_t atomK16 = (uint32_t)(kp * 128) >> 4;   // one K-atom of kp rows, in 16-byte units
+    bool ok = nbr > 0 && __all_sync(0xffffffffu, fu_wait(&bars.onceT, 0u, &s_abort, S.status, lim));
+    auto mma1 = [&](int j) -> bool {
+      const int s = j & 1;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.fafull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim)))
+        return false;
+      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.buffree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
+                                                       S.status, lim)))
+        return false;
+      fence_after_sync();
+      if (elect_one()) {
+        for (int ks = 0; ks < kp / 8; ++ks)
+          mma_tf32_ts(tbase + FT_BUF + 128u * s, tbase + FT_W + 8u * ks, dFa + (uint64_t)(s * (FU_TB >> 4)) + 2u * ks,
+                      id1, ks > 0);
+        mma_commit(&bars.tfull[s]);
+        mma_commit(&bars.fafree[s]);
+      }
+      __syncwarp();
+      return true;
+    };
+    auto hmma = [&](int j) -> bool {
+      const int s = j & 1;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.stashfull, (uint32_t)j & 1u, &s_abort, S.status, lim))) return false;
+      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.haccfree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
+                                                       S.status, lim)))
+        return false;
+      fence_after_sync();
+      if (elect_one()) {
+        const uint32_t acc = tbase + FT_HACC + 64u * s;
+        for (int st = 0; st < 8; ++st) {               // K = 128 rows f in steps of 16
+          const uint64_t ka = 1024u * (st >> 2) + 2u * (st & 3);
+          const uint64_t kb = (uint64_t)atomK16 * (st >> 2) + 2u * (st & 3);
+          mma_bf16(acc, dSA + ka, dWb + kb, idk, st > 0);
+          mma_bf16(acc + 32u, dSB + ka, dWb + kb, idk, st > 0);
+        }
+        mma_commit(&bars.stashfree);
+        mma_commit(&bars.haccfull[s]);
+      }
+      __syncwarp();
+      return true;
+    };
+    auto wmma = [&](int j) -> bool {
+      const int s = j & 1;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.chiready[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim)))
+        return false;
+      fence_after_sync();
+      if (elect_one()) {
+        const uint32_t buf = tbase + FT_BUF + 128u * s;
+        const uint64_t c1 = dChi + (uint64_t)(s * (L.chiSlot >> 4)), c2 = c1 + 2u * atomK16;
+        for (int st = 0; st < 8; ++st) {               // K = 128 columns n in steps of 16
+          const uint32_t a = buf + 32u * (st >> 1) + 16u * (st & 1);
+          const uint64_t kb = (uint64_t)atomK16 * (st >> 2) + 2u * (st & 3);
+          const uint32_t acc = (j > 0 || st > 0) ? 1u : 0u;
+          mma_bf16_ts(tbase + FT_P, a, c1 + kb, idk, acc);
+          mma_bf16_ts(tbase + FT_Q, a + 8u, c2 + kb, idk, acc);
+        }
+        mma_commit(&bars.buffree[s]);
+      }
+      __syncwarp();
+      return true;
+    };
+    if (ok) ok = mma1(0);
+    if (ok && nbr > 1) ok = mma1(1);
+    for (int j = 0; ok && j < nbr; ++j) {
+      ok = hmma(j);
+      if (ok && j >= 1) ok = wmma(j - 1);
+      if (ok && j >= 1 && j + 1 < nbr) ok = mma1(j + 1);
+    }
+    if (ok && nbr > 0) wmma(nbr - 1);
+    if (elect_one()) mma_commit(&bars.done);
+    __syncwarp();
+  } else if (warp >= FU_EPI0 && warp < FU_EX0) {
+    // ---------------- epilogue ----------------
+    // Group g (0, 1) takes tiles g, g + 2 of every batch; warp (q4, half) owns
+    // TMEM lanes 32 q4 .. + 31 (rows f) and columns 16 half .. + 15 of a tile.
+    const int ew = warp - FU_EPI0, q4 = warp & 3, g = (ew >> 2) & 1, half = ew >> 3;
+    const int mrow = 32 * q4 + lane;
+    const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
+    const bool mvalid = m0 + mrow < P.F;
+    const int jb0 = 16 * half;
+    const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
+    // this thread's place in the transposed copies: K-atom mrow / 64, element mrow % 64 (pairs: even element)
+    const uint32_t atomOff = (uint32_t)(mrow >> 6) * 16384u, ePair = (uint32_t)(mrow & 62);
+    const bool odd = lane & 1;
+    if (ew < 4 && nbr > 0) {
+      // warps 4-7 move the W~ rows (MMA1's A operand, kp columns) from shared memory to TMEM
+      if (__all_sync(0xffffffffu, fu_wait(&bars.once, 0u, &s_abort, S.status, lim))) {
+        for (int k0 = 0; k0 < kp; k0 += 16) {
+          float o[16];
+          #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 v4 = *reinterpret_cast<const float4*>(base + L.sa + sw128_offset(mrow, 4 * k0 + 16 * i));
+            o[4 * i] = v4.x; o[4 * i + 1] = v4.y; o[4 * i + 2] = v4.z; o[4 * i + 3] = v4.w;
+          }
+          tmem_st16(tbase + FT_W + lane_off + k0, o);
+        }
+        tmem_st_wait();
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.onceT);
+      }
+    }
+    for (int t = g; t < 4 * nbr; t += 2) {
+      const int j = t >> 2, q = t & 3, s = j & 1;
+      const int sv = t % nv;
+      const uint32_t col = FT_BUF + 128u * s + 32u * q + jb0;
+      // A group starts a new batch only once the previous batch's H contraction
+      // has completed. It then also may overwrite the transposed copies; and on
+      // GB300 a first tile whose TMEM reads and writes overlapped that
+      // contraction (and the other group's last tile of the previous batch)
+      // came out wrong in some runs, which this ordering removes.
+      if (q == g && j >= 1 &&
+          !__all_sync(0xffffffffu, fu_wait(&bars.stashfree, (uint32_t)(j - 1) & 1u, &s_abort, S.status, lim)))
+        break;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.tfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim))) break;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.vfull[sv], (uint32_t)(t / nv) & 1u, &s_abort, S.status, lim))) break;
+      fence_after_sync();
+      float vt[16], vv[16];
+      tmem_ld16(tbase + col + lane_off, vt);
+      const unsigned char* vb = base + L.v0 + sv * FU_TB;
+      #pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v4 = *reinterpret_cast<const float4*>(vb + sw128_offset(mrow, 4 * jb0 + 16 * i));
+        vv[4 * i] = v4.x; vv[4 * i + 1] = v4.y; vv[4 * i + 2] = v4.z; vv[4 * i + 3] = v4.w;
+      }
+      tmem_ld_wait();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.vempty[sv]);
+      const int64_t n1 = 128 * (int64_t)(b0 + j) + 32 * q + jb0;   // first column of this thread's 16
+      const int nvalid = (int)(P.N - n1 < 16 ? (P.N - n1 > 0 ? P.N - n1 : 0) : 16);
+      float tl = 0.f;
+      if (mvalid && nvalid == 16) {
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) epi_terms<BK>(vv[i] + kappa, vt[i] + kappa, bm2, bp, true, tl, vv[i], vt[i]);
+      } else {
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float v = vv[i] + kappa, y = vt[i] + kappa;
+          vv[i] = 0.f;
+          vt[i] = 0.f;
+          if (mvalid && i < nvalid) epi_terms<BK>(v, y, bm2, bp, true, tl, vv[i], vt[i]);
+        }
+      }
+      // A (vv) and B (vt) as bf16 pairs over this thread's Vt columns: [A | B]
+      float cells[16];
+      #pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        cells[p] = __uint_as_float(pack_bf16(vv[2 * p], vv[2 * p + 1]));
+        cells[8 + p] = __uint_as_float(pack_bf16(vt[2 * p], vt[2 * p + 1]));
+      }
+      tmem_st16(tbase + col + lane_off, cells);
+      // neighbouring lanes (rows f, f + 1) exchange values so that each writes
+      // one 32-bit pair: even lanes row n = .. + i, odd lanes row n = .. + i + 1
+      #pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const float ra = __shfl_xor_sync(0xffffffffu, odd ? vv[i] : vv[i + 1], 1);
+        const float rb = __shfl_xor_sync(0xffffffffu, odd ? vt[i] : vt[i + 1], 1);
+        const uint32_t n = (uint32_t)(32 * q + jb0 + i + (odd ? 1 : 0));
+        const uint32_t off = atomOff + sw_bf16(n, ePair);       // (sw_bf16 includes the row offset n * 128)
+        *reinterpret_cast<uint32_t*>(base + L.sa + off) = odd ? pack_bf16(ra, vv[i + 1]) : pack_bf16(vv[i], ra);
+        *reinterpret_cast<uint32_t*>(base + L.sb + off) = odd ? pack_bf16(rb, vt[i + 1]) : pack_bf16(vt[i], rb);
+      }
+      ff_add(lossHi, lossLo, tl);
+      tmem_st_wait();
+      fence_before_sync();
+      fence_smem_to_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.stashfull);
+    }
+  } else if (warp >= FU_EX0) {
+    // ---------------- cluster exchange ----------------
+    // Thread x (0..127) owns TMEM lane x = column x of the batch for the
+    // mailbox write. The batch's K x 32 tasks (row k, four columns 4u .. 4u
+    // + 3; task t = 32 k + u) are split evenly over the cluster's blocks:
+    // block r reduces tasks [32 K r / c, 32 K (r + 1) / c).
+    // Each warp publishes what it wrote itself (warp barrier, one fence at
+    // cluster scope, relaxed arrivals; the cluster barriers count 4 c
+    // arrivals), so the four warps never wait for one another.
+    const int x = tid - FU_EX0 * 32;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int tLo = 32 * K * r / c, ntask = 32 * K * (r + 1) / c - tLo;
+    const uint32_t mbS = smem_u32(base + L.mb);
+    const float gam = (float)bp.gamma, flo = (float)bp.floor, beta = (float)bp.beta;
+    float* mb = reinterpret_cast<float*>(base + L.mb);
+    for (int j = 0; j < nbr; ++j) {
+      const int s = j & 1;
+      // The mailbox is rewritten only after this block has received every
+      // owner's chi of the previous batch (which the owners sent after
+      // reading it), and chi slot s of every block is free once the mailbox
+      // handshake of batch j completes: each block writes its mailbox after
+      // its H contraction of batch j, whose completion covers its W
+      // contraction of batch j - 2. So two handshakes per batch suffice.
+      bool go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim));
+      if (go) {
+        fence_after_sync();
+        for (int k0 = 0; k0 < kp; k0 += 16) {
+          float hn[16], hd[16];
+          tmem_ld16(tbase + FT_HACC + 64u * s + lane_off + k0, hn);
+          tmem_ld16(tbase + FT_HACC + 64u * s + 32u + lane_off + k0, hd);
+          tmem_ld_wait();
+          #pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (k0 + i < K) {
+              mb[(k0 + i) * 128 + x] = hn[i];
+              mb[(K + k0 + i) * 128 + x] = hd[i];
+            }
+        }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.haccfree[s]);
+        // each warp publishes its own columns: warp barrier (cumulative), one
+        // fence at cluster scope, relaxed arrivals
+        __syncwarp();
+        if (lane == 0 && !s_abort) {
+          fence_acq_rel_cluster();
+          for (int q = 0; q < c; ++q) mbar_arrive_remote_relaxed(dsmem_map(&bars.mailfull[s], (uint32_t)q));
+        }
+      }
+      const int64_t nb0 = 128 * (int64_t)(b0 + j);
+      // this thread's H~ values (one task, four columns; they do not depend
+      // on the exchange) load while the other blocks' partials arrive
+      float htp[4];
+      {
+        const int task = x, k = (tLo + task) >> 5, n4 = 4 * ((tLo + task) & 31);
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t n = nb0 + n4 + i;
+          htp[i] = (task < ntask && n < P.N) ? __ldg(&P.Ht[(int64_t)k * P.N + n]) : 1.f;
+        }
+      }
+      float hkeep[4] = {0.f, 0.f, 0.f, 0.f};
+      go = !s_abort && __all_sync(0xffffffffu, fu_wait_cluster(&bars.mailfull[s], (uint32_t)(j >> 1) & 1u, &s_abort,
+                                                               S.status, lim));
+      // tasks of (row k, 4 columns): the four columns' numerators and
+      // denominators of up to four ranks in flight together, summed in rank order
+      for (int task = x; go && task < ntask; task += 128) {
+        const int k = (tLo + task) >> 5, n4 = 4 * ((tLo + task) & 31);
+        const uint32_t on = mbS + (uint32_t)(k * 512 + 4 * n4), od = mbS + (uint32_t)((K + k) * 512 + 4 * n4);
+        float ht[4];
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t n = nb0 + n4 + i;
+          ht[i] = task == x ? htp[i] : (n < P.N ? __ldg(&P.Ht[(int64_t)k * P.N + n]) : 1.f);
+        }
+        float hn[4] = {0.f, 0.f, 0.f, 0.f}, hd[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q0 = 0; q0 < c; q0 += 4) {
+          float4 pn[4], pd[4];
+          #pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u < c) {
+              pn[u] = dsmem_ld4(dsmem_map_addr(on, (uint32_t)(q0 + u)));
+              pd[u] = dsmem_ld4(dsmem_map_addr(od, (uint32_t)(q0 + u)));
+            }
+          #pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u < c) {
+              hn[0] += pn[u].x; hn[1] += pn[u].y; hn[2] += pn[u].z; hn[3] += pn[u].w;
+              hd[0] += pd[u].x; hd[1] += pd[u].y; hd[2] += pd[u].z; hd[3] += pd[u].w;
+            }
+        }
+        float c1[4], c2[4];
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t n = nb0 + n4 + i;
+          c1[i] = c2[i] = 0.f;
+          if (n < P.N) {
+            const float h = apply_floor(ht[i] * mu_ratio<BK, float>(hn[i], hd[i], gam), flo);
+            if (!isfinite(h)) atomicExch(S.status, 4);
+            if (task == x) hkeep[i] = h;            // this thread's first task: stored after the handshake
+            else P.H[(int64_t)k * P.N + n] = h;
+            chi_terms<BK, float>(h, ht[i], beta, c1[i], c2[i]);
+          }
+        }
+        // chi rows k, columns n4 .. n4 + 3: 8 bytes of a 16-byte chunk of K-atom n4 / 64
+        const uint32_t off = L.chi0 + s * L.chiSlot + (uint32_t)(n4 >> 6) * (kp * 128u) + (uint32_t)k * 128u +
+                             ((((uint32_t)(n4 & 63) >> 3) ^ ((uint32_t)k & 7u)) << 4) + (uint32_t)(n4 & 4) * 2u;
+        const uint32_t dst = smem_u32(base + off);
+        const uint32_t a1 = pack_bf16(c1[0], c1[1]), b1 = pack_bf16(c1[2], c1[3]);
+        const uint32_t a2 = pack_bf16(c2[0], c2[1]), b2 = pack_bf16(c2[2], c2[3]);
+        for (int q = 0; q < c; ++q) {
+          dsmem_st2u(dsmem_map_addr(dst, (uint32_t)q), a1, b1);
+          dsmem_st2u(dsmem_map_addr(dst + 2u * kp * 128u, (uint32_t)q), a2, b2);
+        }
+      }
+      fence_smem_cluster_to_async();
+      __syncwarp();
+      if (lane == 0 && !s_abort) {
+        fence_acq_rel_cluster();
+        for (int q = 0; q < c; ++q) mbar_arrive_remote_relaxed(dsmem_map(&bars.chifull[s], (uint32_t)q));
+      }
+      {                                             // H of this thread's first task, now off the fence's path
+        const int task = x, k = (tLo + task) >> 5, n4 = 4 * ((tLo + task) & 31);
+        if (go && task < ntask)
+          #pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (nb0 + n4 + i < P.N) P.H[(int64_t)k * P.N + nb0 + n4 + i] = hkeep[i];
+      }
+      go = !s_abort &&
+           __all_sync(0xffffffffu, fu_wait_cluster(&bars.chifull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim));
+      fence_smem_to_async();
+      __syncwarp();
+      if (lane == 0 && go && !s_abort) mbar_arrive(&bars.chiready[s]);   // one arrival per exchange warp
+    }
+    // (no block touches this block's shared memory after the last chi
+    // handshake: the owners read its mailbox before pushing their chi)
+  }
+
+  // ---------------- P, Q: one partial slice per cluster ----------------
+  // Epilogue thread (mrow, grp) owns kp / 2 columns of P (grp 0, 1) or Q
+  // (grp 2, 3) in TMEM lane mrow; the rows go out through shared memory (the
+  // A^T, B^T copies are idle once every MMA is done) as two contiguous runs.
+  const bool epi = warp >= FU_EPI0 && warp < FU_EX0;
+  const int grp = (warp - FU_EPI0) >> 2, mrow = 32 * (warp & 3) + lane;
+  const int per = kp / 2;
+  const bool isQ = grp >= 2;
+  const int col0 = (grp & 1) * per;
+  bool have = false;
+  if (epi) {
+    have = nbr > 0 && !s_abort && fu_wait(&bars.done, 0u, &s_abort, S.status, lim);
+    have = __all_sync(0xffffffffu, have);
+  }
+  float acc[16];
+  #pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  if (epi && have) {
+    fence_after_sync();
+    const uint32_t ta = tbase + (isQ ? FT_Q : FT_P) + ((uint32_t)(32 * (warp & 3)) << 16) + col0;
+    tmem_ld8(ta, acc);
+    if (per > 8) tmem_ld8(ta + 8, acc + 8);
+    tmem_ld_wait();
+  }
+  const int Ks = K | 1;
+  float* stg = reinterpret_cast<float*>(base + L.sa);
+  __syncthreads();
+  const bool write = __syncthreads_or(have ? 1 : 0) != 0;
+  if (epi && have) {
+    float* row = stg + (isQ ? 128 * Ks : 0) + mrow * Ks + col0;
+    #pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < per && col0 + i < K) row[i] = acc[i];
+  }
+  __syncthreads();
+  if (write) {
+    const int nrows = (int)(P.F - m0 < 128 ? P.F - m0 : 128);
+    float* outP = P.rowPart + (int64_t)cl * 2 * P.F * K + m0 * K;
+    float* outQ = outP + P.F * K;
+    for (int rr = warp; rr < nrows; rr += FU_THREADS / 32)
+      for (int cc = lane; cc < K; cc += 32) {
+        outP[rr * K + cc] = stg[rr * Ks + cc];
+        outQ[rr * K + cc] = stg[128 * Ks + rr * Ks + cc];
+      }
+  }
+  const double unitLoss = block_sum_ff(lossHi, lossLo, reinterpret_cast<float2*>(red));
+  if (tid == 0) S.lossPart[blockIdx.x] = unitLoss;
+  fence_before_sync();
+  __syncthreads();
+  if (s_abort) mbar_wait(&bars.done, 0u, 100000000ull);
+  // no block leaves while another may still arrive on or read its barriers
+  cluster_sync();
+  if (warp == 2) tmem_dealloc(tbase, FT_COLS);
+}
+
+}  // namespace
+
+// ---- host ------------------------------------------------------------------
+
+bool tc_fused_supported(const Prob<float>& P) {
+  return P.sWS && P.kp <= 32 && P.F <= 1024 && fu_pick_nv(P.K, P.kp) >= 2;
+}
+
+int tc_fused_clusters(const Prob<float>& P, int sms) {
+  const int c = (int)((P.F + 127) / 128);
+  const int nbatch = (int)((P.N + 127) / 128);
+  const int nv = fu_pick_nv(P.K, P.kp);
+  const size_t sm = 1024 + fu_layout(P.K, P.kp, nv).total;
+  auto kern = tc_fused_kernel<BK_GENERAL>;
+  if (ensure_smem_attr(reinterpret_cast<const void*>(kern), sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(c * ((sms + c - 1) / c)));
+  cfg.blockDim = dim3(FU_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // NMF_FU_CLUSTERS=<n>: at most n clusters (each then runs more batches; for tests and tuning)
+  const char* env = std::getenv("NMF_FU_CLUSTERS");
+  if (env && std::atoi(env) > 0 && std::atoi(env) < n) n = std::atoi(env);
+  return n < nbatch ? n : nbatch;
+}
+
+cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
+                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st) {
+  FuParams S;
+  memset(&S, 0, sizeof(S));
+  S.c = (int)((P.F + 127) / 128);
+  S.nbatch = (int)((P.N + 127) / 128);
+  S.ncl = ncl;
+  S.nv = fu_pick_nv(P.K, P.kp);
+  S.lossPart = lossPart;
+  S.status = status;
+  S.limitNs = limitNs;
+  S.extra = extra;
+  if (S.nv < 2 || ncl < 1 || ncl > S.nbatch || S.c > 8) return cudaErrorInvalidValue;
+  CUtensorMap tmV;
+  if (!tc_map_v(P, true, &tmV)) return cudaErrorInvalidValue;   // V rows must be 16-byte aligned (the context pads them)
+  const size_t sm = 1024 + fu_layout(P.K, P.kp, S.nv).total;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(S.c * ncl));
+  cfg.blockDim = dim3(FU_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S.c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaError_t e = cudaSuccess;
+#define NMF_FU_CASE(BKV)                                                                   \
+  case BKV:                                                                                \
+    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV>), sm);         \
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV>, tmV, m.wsA, m.htB, P, bp, S); \
+    break;
+  switch (bp.kind) {
+    NMF_FU_CASE(BK_IS)
+    NMF_FU_CASE(BK_KL)
+    NMF_FU_CASE(BK_EUC)
+    NMF_FU_CASE(BK_B15)
+    NMF_FU_CASE(BK_GENERAL)
+  }
+#undef NMF_FU_CASE
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace nmf

@@ -91,6 +91,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       :: "r"(d_tmem), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
 }
+// kind::f16 (both operands bf16) with the A operand in tensor memory: each
+// 32-bit column of an M x 16 A block holds two consecutive K elements, the
+// lower K index in the low half.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+      :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(id), "r"(acc) : "memory");
+}
 // Arrives on the mbarrier once every MMA issued so far by this thread is done.
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -204,8 +213,59 @@ __device__ __forceinline__ uint32_t dsmem_map(const void* local, uint32_t rank) 
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
   return r;
 }
+// Same for a 32-bit shared-memory address of this block.
+__device__ __forceinline__ uint32_t dsmem_map_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
 __device__ __forceinline__ void dsmem_st4(uint32_t addr, float a, float b, float c, float d) {
   asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Arrival, with release semantics at cluster scope, on an mbarrier of block
+// `rank` of the cluster (remote = dsmem_map of the local barrier's address).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t remote) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(remote) : "memory");
+}
+// Relaxed arrival on a barrier of block `rank` of the cluster: cheaper than a
+// release arrival per barrier; the caller orders its (and, through a block
+// barrier, other threads') earlier writes with one fence.acq_rel.cluster first.
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t remote) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" :: "r"(remote) : "memory");
+}
+// try_wait with acquire semantics at cluster scope: once it returns true, the
+// writes other blocks made before their (release) arrivals are visible.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ float4 dsmem_ld4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void dsmem_st4u(uint32_t addr, uint4 v) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void dsmem_st2u(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" :: "r"(addr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+// Generic-proxy writes (local or another block's shared memory) -> visible to
+// the async proxy (tensor core operand reads).
+__device__ __forceinline__ void fence_smem_cluster_to_async() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+// Named barrier over `count` threads (multiple of 32) of this block.
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+  asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(count) : "memory");
 }
 
 // ---- TMEM loads -------------------------------------------------------------

@@ -1,0 +1,193 @@
+"""The fused single-read JMM iteration (NMF_BF16, tc_fused.cu) against the
+FP64 oracle.
+
+One launch per iteration reads V once: the product in TF32, A and B once,
+both contractions from on-chip bf16 copies of A and B (H first, L = 1; the
+inverted update order of Sec. 4.1.1), the H partials exchanged inside a
+cluster of ceil(F / 128) blocks. Tolerances (derived in the design notes):
+3e-2 relative on W and H after one iteration (bf16 operands, u = 2^-9, in
+both contractions and the MU ratio), 5e-3 on the objective at the iterate
+(its terms use the TF32 product, as on the TF32 path).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_15214_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_WH, TOL_D = 3e-2, 5e-3
+
+
+def problem(F, N, K, seed):
+    rng = np.random.default_rng(seed)
+    V = rng.gamma(1.0, 1.0, (F, K)) @ rng.gamma(1.0, 1.0, (K, N)) + 0.05
+    V = V * rng.uniform(0.5, 1.5, (F, N))
+    W0, H0 = inputs.uniform_init(F, N, K, seed=seed + 7)
+    return V, W0, H0
+
+
+def run_bf16(V, W0, H0, beta, iters=1, order="H", want_loss=True):
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    F, N = V.shape
+    K = W0.shape[1]
+    m = NMF(F, N, K, beta, precision="bf16", order=order)
+    Vd = torch.tensor(V, dtype=torch.float32, device="cuda")
+    W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+    H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+    m.set_dense(Vd)
+    m.set_factors(W, H)
+    loss = m.step_joint(iters, want_loss=want_loss)
+    out = (W.double().cpu().numpy(), H.double().cpu().numpy(), loss)
+    m.close()
+    return out
+
+
+def oracle_h_first(V, W0, H0, beta, iters=1):
+    W, H, losses = O.run(V, W0, H0, beta, iters=iters, order="H", eps=1e-30)
+    return W, H, losses
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.parametrize("shape", [(100, 300, 4), (200, 333, 20), (361, 517, 32), (513, 1000, 20)])
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1.5, 2.0])
+def test_one_iteration_matches_oracle(lib, shape, beta):
+    """Clusters of 1, 2, 3 and 5 blocks; ragged rows (F % 128) and columns (N % 128)."""
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=F + N)
+    W, H, loss = run_bf16(V, W0, H0, beta)
+    Wo, Ho, lo = oracle_h_first(V, W0, H0, beta)
+    assert np.all(np.isfinite(W)) and np.all(np.isfinite(H))
+    assert rel(W, Wo) < TOL_WH
+    assert rel(H, Ho) < TOL_WH
+    assert loss == pytest.approx(lo[0], rel=TOL_D)
+
+
+@pytest.mark.parametrize("beta", [-1.0, 0.5, 3.0])
+def test_general_beta(lib, beta):
+    V, W0, H0 = problem(300, 400, 16, seed=5)
+    W, H, loss = run_bf16(V, W0, H0, beta)
+    Wo, Ho, lo = oracle_h_first(V, W0, H0, beta)
+    assert rel(W, Wo) < TOL_WH and rel(H, Ho) < TOL_WH
+    assert loss == pytest.approx(lo[0], rel=TOL_D)
+
+
+def test_many_iterations_follow_the_oracle(lib):
+    """20 iterations on a spectrogram-shaped problem: the objective stays within
+    5e-3 of the oracle's (the iterates follow a nearby trajectory)."""
+    p = inputs.dense_is_spectrogram(N=2000)
+    W, H, loss = run_bf16(p.V, p.W0, p.H0, 0.0, iters=20)
+    Wo, Ho, lo = oracle_h_first(p.V, p.W0, p.H0, 0.0, iters=20)
+    assert loss == pytest.approx(lo[19], rel=TOL_D)
+    D_gpu = O.D_beta(p.V, W @ H, 0.0)
+    assert D_gpu == pytest.approx(lo[20], rel=TOL_D)
+
+
+def test_full_size_spectrogram(lib):
+    """The spectrogram workload at full size (F = 513, N = 20000, K = 20): one
+    iteration, element-wise against the oracle."""
+    p = inputs.dense_is_spectrogram()
+    W, H, loss = run_bf16(p.V, p.W0, p.H0, 0.0)
+    Wo, Ho, lo = oracle_h_first(p.V, p.W0, p.H0, 0.0)
+    assert rel(W, Wo) < TOL_WH and rel(H, Ho) < TOL_WH
+    assert loss == pytest.approx(lo[0], rel=TOL_D)
+
+
+@pytest.mark.parametrize("shape,ncl", [((513, 2560, 20), 2), ((200, 5000, 32), 3), ((100, 3000, 4), 1)])
+def test_many_batches_per_cluster(lib, shape, ncl):
+    """NMF_FU_CLUSTERS caps the clusters, so each one runs many 128-column
+    batches through the double-buffered pipeline and the cluster handshakes."""
+    import os
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=N)
+    os.environ["NMF_FU_CLUSTERS"] = str(ncl)
+    try:
+        W, H, loss = run_bf16(V, W0, H0, 0.0)
+    finally:
+        del os.environ["NMF_FU_CLUSTERS"]
+    Wo, Ho, lo = oracle_h_first(V, W0, H0, 0.0)
+    assert rel(W, Wo) < TOL_WH and rel(H, Ho) < TOL_WH
+    assert loss == pytest.approx(lo[0], rel=TOL_D)
+
+
+def test_deterministic_and_async_equals_sync(lib):
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    V, W0, H0 = problem(513, 1500, 20, seed=9)
+    outs = []
+    for mode in ("sync", "sync", "async"):
+        m = NMF(513, 1500, 20, 0.0, precision="bf16", order="H")
+        Vd = torch.tensor(V, dtype=torch.float32, device="cuda")
+        W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+        H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+        m.set_dense(Vd)
+        m.set_factors(W, H)
+        if mode == "sync":
+            loss = m.step_joint(3)
+        else:
+            ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+            m.step_joint_async(ld, iters=3)
+            torch.cuda.synchronize()
+            loss = float(ld.item())
+        outs.append((W.cpu().numpy(), H.cpu().numpy(), loss))
+        m.close()
+    for W, H, loss in outs[1:]:
+        assert np.array_equal(W, outs[0][0]) and np.array_equal(H, outs[0][1]) and loss == outs[0][2]
+
+
+def test_unsupported_forms_are_rejected(lib):
+    import torch
+    from paper_2106_15214_gb300.binding import NMF, NMF_EUNSUPPORTED, NMFError
+    V, W0, H0 = problem(64, 96, 4, seed=1)
+    for kw, call in ((dict(order="W"), "joint"), (dict(order="H"), "alternating"), (dict(order="H", L=2), "joint")):
+        m = NMF(64, 96, 4, 1.0, precision="bf16", **kw)
+        m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
+        m.set_factors(torch.tensor(W0, dtype=torch.float32, device="cuda"),
+                      torch.tensor(H0, dtype=torch.float32, device="cuda"))
+        with pytest.raises(NMFError) as e:
+            (m.step_joint if call == "joint" else m.step_alternating)(1)
+        assert e.value.code == NMF_EUNSUPPORTED
+        m.close()
+    m = NMF(64, 96, 40, 1.0, precision="bf16", order="H")       # K > 32
+    Wb, Hb = inputs.uniform_init(64, 96, 40, seed=2)
+    m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
+    m.set_factors(torch.tensor(Wb, dtype=torch.float32, device="cuda"),
+                  torch.tensor(Hb, dtype=torch.float32, device="cuda"))
+    with pytest.raises(NMFError) as e:
+        m.step_joint(1)
+    assert e.value.code == NMF_EUNSUPPORTED
+    m.close()
+
+
+def test_cluster_wait_timeout_returns_etimeout(lib):
+    """The cluster exchange's waits expect one arrival more than there are
+    blocks (nmf_set_barrier_test): every such wait runs out after 2 ms, the
+    step returns NMF_ETIMEOUT with W and H restored, and the context then
+    computes the oracle's iterate with the defaults back."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF, NMF_ETIMEOUT, NMFError, check
+    V, W0, H0 = problem(200, 333, 20, seed=3)
+    m = NMF(200, 333, 20, 1.0, precision="bf16", order="H")
+    Vd = torch.tensor(V, dtype=torch.float32, device="cuda")
+    W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+    H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+    W1, H1 = W.clone(), H.clone()
+    m.set_dense(Vd)
+    m.set_factors(W, H)
+    check(lib.nmf_set_barrier_test(m._ctx, 2_000_000, 1), "nmf_set_barrier_test")
+    with pytest.raises(NMFError) as e:
+        m.step_joint(1)
+    assert e.value.code == NMF_ETIMEOUT
+    torch.cuda.synchronize()
+    assert torch.equal(W, W1) and torch.equal(H, H1)
+    check(lib.nmf_set_barrier_test(m._ctx, 1_000_000_000, 0), "nmf_set_barrier_test")
+    m.set_factors(W, H)
+    m.step_joint(1)
+    Wo, Ho, _ = oracle_h_first(V, W0, H0, 1.0)
+    assert rel(W.double().cpu().numpy(), Wo) < TOL_WH and rel(H.double().cpu().numpy(), Ho) < TOL_WH
+    m.close()
