@@ -1,14 +1,18 @@
 #!/usr/bin/env python
 """Joint-MM beta-NMF benchmark on one GB300 (replicas on N GPUs).
 
-Default workload: dense quadratic-loss NMF (beta = 2) shaped like a face-image
-collection, F = 361 (19 x 19 pixels), N = 2429 images, K = 49; synthetic data
-(paper_2106_15214_gb300.inputs.dense_quadratic_faces). One step is one outer
-JMM iteration (Algorithm 2, L = 1): the product at the iterate, both factor
-updates, the objective at the iterate and the normalisation. The metric is
-JMM iterations/s; beside it: the dominant kernel's roofline, the host-buffer
-end-to-end rate, the CPU oracle's rate, and the time to the paper's stopping
-tolerance of JMM against alternating MU (BMM) on the same GPU.
+Default workload: dense Itakura-Saito NMF (beta = 0) shaped like an audio
+power spectrogram, F = 513 frequency bins, N = 20000 frames, K = 20;
+synthetic data (paper_2106_15214_gb300.inputs.dense_is_spectrogram). One step
+is one outer JMM iteration (Algorithm 2, L = 1, H first): the product at the
+iterate, both factor updates, the objective at the iterate and the
+normalisation, on the fused single-read path (TF32 product, bf16
+contractions). The metric is JMM iterations/s; beside it: the dominant
+kernel's and the whole step's HBM roofline, the host-buffer end-to-end rate,
+the CPU oracle's rate, the time to fixed objective targets D* and to the
+paper's stopping rule of JMM against alternating MU (BMM) on the same GPU,
+and extra workloads (the same problem at N = 200000, the TF32 two-sweep
+form, sparse KL count data, 512 batched problems).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -30,12 +34,15 @@ METRIC = "joint-MM iters/s"
 L2_FLUSH_BYTES = 512 << 20
 
 WORKLOADS = {
-    "faces": dict(gen="dense_quadratic_faces", beta=2.0, desc="dense quadratic (beta=2) faces F=361 N=2429 K=49"),
-    "spectrogram": dict(gen="dense_is_spectrogram", beta=0.0, desc="dense Itakura-Saito (beta=0) F=513 N=20000 K=20"),
-    # V = 410 MB, well above the 129 MB L2: every sweep streams V from HBM
-    "spectrogram_large": dict(gen="dense_is_spectrogram", kw={"N": 200000}, beta=0.0,
+    "spectrogram": dict(gen="dense_is_spectrogram", beta=0.0, precision="bf16", order="H",
+                        desc="dense Itakura-Saito (beta=0) F=513 N=20000 K=20"),
+    # V = 410 MB, well above the 129 MB L2: every read of V comes from HBM
+    "spectrogram_large": dict(gen="dense_is_spectrogram", kw={"N": 200000}, beta=0.0, precision="bf16", order="H",
                               desc="dense Itakura-Saito (beta=0) F=513 N=200000 K=20"),
-    "kl_small": dict(gen="dense_kl_small", beta=1.0, desc="dense KL (beta=1) F=200 N=500 K=10"),
+    "faces": dict(gen="dense_quadratic_faces", beta=2.0, precision="tf32", order="W",
+                  desc="dense quadratic (beta=2) faces F=361 N=2429 K=49"),
+    "kl_small": dict(gen="dense_kl_small", beta=1.0, precision="fp64", order="W",
+                     desc="dense KL (beta=1) F=200 N=500 K=10"),
 }
 
 
@@ -45,14 +52,6 @@ WORKLOADS = {
 # launch. Sources and commands: the traffic summaries under profiles/. An
 # entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    ("faces", "tf32", "W", "tc_row_sweep"): 4920320,
-    ("faces", "tf32", "W", "rows_epilogue"): 5478912,
-    ("faces", "tf32", "W", "tc_col_sweep"): 4515840,
-    ("faces", "tf32", "W", "cols_epilogue"): 6276864,
-    ("spectrogram", "tf32", "W", "tc_row_sweep"): 46302976,
-    ("spectrogram", "tf32", "W", "rows_epilogue"): 2534400,
-    ("spectrogram", "tf32", "W", "tc_col_sweep"): 43898112,
-    ("spectrogram", "tf32", "W", "cols_epilogue"): 7789056,
 }
 
 
@@ -62,13 +61,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="faces", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, help="tf32 (default) | fp32 | fp64")
-    ap.add_argument("--order", default="W")
+    ap.add_argument("--workload", default="spectrogram", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, help="bf16 | tf32 | fp32 | fp64 (default: the workload's)")
+    ap.add_argument("--order", default=None, help="W | H (default: the workload's)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target and stopping-rule runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--max-ttt-iters", type=int, default=10000)
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--max-ttt-iters", type=int, default=6000)
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="skip the per-kernel timing pass (no roofline, no launch count)")
     return ap.parse_args()
@@ -91,21 +91,20 @@ def cpu_threads():
     return os.cpu_count() or 1
 
 
-def time_oracle(p, beta, seconds, max_iters=None, warmup=1):
-    """Oracle JMM iterations (as written, no tuning) on the host cores."""
+def time_oracle(p, beta, seconds, order="H", warmup=1):
+    """Oracle JMM iterations (as written, no tuning) of the whole workload on
+    the host cores, for about `seconds`; returns (iterations, seconds)."""
     import oracle as O
     W, H = p.W0.copy(), p.H0.copy()
     for _ in range(warmup):
-        W, H = O.jmm_iteration(p.V, W, H, beta)
-        W, H = O.normalize(W, H)
+        W, H = O.normalize(*O.jmm_iteration(p.V, W, H, beta, order=order))
     n, t0 = 0, time.perf_counter()
     while True:
         _ = O.D_beta(p.V, W @ H, beta)
-        W, H = O.jmm_iteration(p.V, W, H, beta)
-        W, H = O.normalize(W, H)
+        W, H = O.normalize(*O.jmm_iteration(p.V, W, H, beta, order=order))
         n += 1
         el = time.perf_counter() - t0
-        if el >= seconds or (max_iters and n >= max_iters):
+        if el >= seconds:
             return n, el
 
 
@@ -217,62 +216,82 @@ def aggregate_rate(world, steps, max_seconds):
     return world * steps / max_seconds
 
 
-def algorithmic_bytes(kernel, F, N, K, esize=4):
+def algorithmic_bytes(kernel, F, N, K, esize=4, order="W"):
     """Minimal DRAM bytes one launch of `kernel` must move: V once, every
-    factor-sized operand it reads once, what it writes once. Partial-sum
+    distinct factor-sized operand it reads once (H~ counts once although the
+    tensor-core kernels read it in two layouts; the tensor-core copies of a
+    factor are not separate operands), what it writes once. Partial-sum
     slices from splitting the streamed dimension are not counted (they are
-    the kernel's choice, not the algorithm's)."""
+    the kernel's choice)."""
     V = F * N * esize
     FK, KN = F * K * esize, K * N * esize
+    wfirst = order != "H"
+    first_row = V + FK + KN + 2 * FK               # W half first: V, W~, H~ in; P, Q out
+    second_col = V + FK + KN + 2 * FK + 2 * KN     # then: V, W~, H~, chi_1(W), chi_2(W) in; Hn, Hd out
+    first_col = V + FK + KN + 2 * KN               # H half first: V, W~, H~ in; Hn, Hd out
+    second_row = V + FK + KN + 2 * KN + 2 * FK     # then: V, W~, H~, chi_1(H), chi_2(H) in; P, Q out
     table = {
-        # Vt tile operand (W~), the MMA1 operand (H~), the two contraction operands (H~ or chi(H)); P, Q out
-        "row_sweep": V + FK + 3 * KN + 2 * FK,
-        "tc_row_sweep": V + FK + 3 * KN + 2 * FK,
-        # H~, W~, chi(W) twice; Hn, Hd out
-        "col_sweep": V + 3 * FK + KN + 2 * KN,
-        "tc_col_sweep": V + 3 * FK + KN + 2 * KN,
-        # P, Q and W~ in; W, chi_1(W), chi_2(W) and their two tensor-core copies out
-        "rows_epilogue": 8 * FK,
-        # W first, the iteration's last kernel: Hn, Hd and H~ in; H, H~ and the
-        # two tensor-core copies of H out; W in; W, W~ and W's two copies out
-        "cols_epilogue": 7 * KN + 5 * FK,
-        # W, H in; W~, H~ and two tensor-core copies of each out
-        "begin_iteration": 4 * (FK + KN),
+        "row_sweep": first_row if wfirst else second_row,
+        "tc_row_sweep": first_row if wfirst else second_row,
+        "col_sweep": second_col if wfirst else first_col,
+        "tc_col_sweep": second_col if wfirst else first_col,
+        # one read of V: V, W~ rows, H~ in; H out; P, Q out once
+        "tc_fused": V + FK + KN + KN + 2 * FK,
+        # P, Q and W~ in, W out; W first also chi_1(W), chi_2(W) out
+        "rows_epilogue": 6 * FK if wfirst else 4 * FK,
+        # W first, the iteration's last kernel: Hn, Hd and H~ in; H out; W in;
+        # W and W~ out (normalisation)
+        "cols_epilogue": 4 * KN + 3 * FK,
+        # W, H in; W~, H~ out
+        "begin_iteration": 2 * (FK + KN),
         "normalize": 2 * (FK + KN),
     }
     return table.get(kernel)
 
 
+def step_bytes(F, N, K, esize=4):
+    """Algorithmic bytes of one JMM iteration: V read once, both factors read
+    and written once."""
+    return esize * (F * N + 2 * (F + N) * K)
+
+
 def run_reference(args):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The oracle on the host cores, each step one JMM iteration on a sample of
+    the workload's columns sized so that the K + W steps take about a minute;
+    the rate is scaled to whole-workload iterations (the work is linear in N)."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle as O
     p, wl = problem(args.workload)
     beta = wl["beta"]
-    W, H = p.W0.copy(), p.H0.copy()
+    order = args.order or wl["order"]
+    F, N, K = p.shape
+    t0 = time.perf_counter()
+    O.normalize(*O.jmm_iteration(p.V, p.W0, p.H0, beta, order=order))
+    t_full = time.perf_counter() - t0
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    Ns = int(max(32, min(N, round(N * budget / max(t_full, 1e-9)))))
+    V, W, H = p.V[:, :Ns], p.W0.copy(), p.H0[:, :Ns].copy()
     for _ in range(args.warmup):
-        W, H = O.jmm_iteration(p.V, W, H, beta)
-        W, H = O.normalize(W, H)
+        W, H = O.normalize(*O.jmm_iteration(V, W, H, beta, order=order))
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _ = O.D_beta(p.V, W @ H, beta)
-        W, H = O.jmm_iteration(p.V, W, H, beta)
-        W, H = O.normalize(W, H)
+        _ = O.D_beta(V, W @ H, beta)
+        W, H = O.normalize(*O.jmm_iteration(V, W, H, beta, order=order))
         times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    val = args.steps / tot
-    F, N, K = p.shape
+    val = (Ns / N) * args.steps / sum(times)
+    sample = (f"{args.steps} JMM iterations (objective, both updates, normalisation; numpy FP64 oracle) on the "
+              f"first {Ns} of the {N} columns, rate scaled by {Ns}/{N} to whole-workload iterations")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "iters/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "F": F, "N": N, "K": K, "beta": beta,
+        "config": {"workload": wl["desc"], "F": F, "N": N, "K": K, "beta": beta, "order": order,
                    "step": "one JMM outer iteration (L=1) with objective and normalisation"},
-        "cpu_baseline": {"value": val, "unit": "iters/s", "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} full JMM iterations of the workload (numpy FP64 oracle)"},
+        "cpu_baseline": {"value": val, "unit": "iters/s", "cores": cpu_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -294,7 +313,22 @@ def timing_records(m):
     return recs, n.value
 
 
-def time_to_tolerance(p, beta, precision, method, tol, max_iters, order="W"):
+def fp64_objective(p, beta, W, H):
+    """D_beta(V | WH) of (W, H) evaluated by the FP64 path on the GPU."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    F, N, K = p.shape
+    m = NMF(F, N, K, beta, precision="fp64")
+    V64 = torch.tensor(p.V, dtype=torch.float64, device="cuda")
+    W64, H64 = W.double().contiguous(), H.double().contiguous()
+    m.set_dense(V64)
+    m.set_factors(W64, H64)
+    d = m.loss()
+    m.close()
+    return d
+
+
+def dense_context(p, beta, precision, order):
     import torch
     from paper_2106_15214_gb300.binding import NMF
     F, N, K = p.shape
@@ -305,12 +339,91 @@ def time_to_tolerance(p, beta, precision, method, tol, max_iters, order="W"):
     H = torch.tensor(p.H0, dtype=dt, device="cuda")
     m.set_dense(V)
     m.set_factors(W, H)
+    return m, V, W, H
+
+
+def time_to_target(p, beta, precision, method, order, targets, max_iters, chunk=25):
+    """Iterations and GPU time until the FP64 objective of the iterate falls
+    to each target D* (targets: label -> value). A search pass (untimed)
+    steps in chunks, evaluates the FP64 objective after each chunk and
+    resolves a crossing by re-running the chunk one iteration at a time from
+    its saved start; the kernels are deterministic, so a second, timed pass
+    from the initial factors runs the same trajectory: the largest count
+    needed, back to back on the stream, with a CUDA event after each target's
+    count."""
+    import torch
+    m, V, W, H = dense_context(p, beta, precision, order)
+    step = m.step_joint_async if method == "jmm" else m.step_alternating_async
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    need, it = {}, 0
+    d_last = fp64_objective(p, beta, W, H)
+    while it < max_iters and len(need) < len(targets):
+        W0c, H0c = W.clone(), H.clone()
+        n = min(chunk, max_iters - it)
+        step(ld, iters=n)
+        d = fp64_objective(p, beta, W, H)
+        crossed = [lb for lb, t in targets.items() if lb not in need and d <= t]
+        if crossed:
+            W.copy_(W0c)
+            H.copy_(H0c)
+            for k in range(1, n + 1):
+                step(ld, iters=1)
+                dk = fp64_objective(p, beta, W, H)
+                for lb in crossed:
+                    if lb not in need and dk <= targets[lb]:
+                        need[lb] = it + k
+                if all(lb in need for lb in crossed):
+                    W.copy_(W0c)
+                    H.copy_(H0c)
+                    step(ld, iters=n)
+                    break
+        it += n
+        d_last = d
+    m.close()
+    out = {"precision": precision, "method": method, "order": order, "iters_searched": it,
+           "D_fp64_search_end": d_last}
+    times = {}
+    if need:
+        m, V, W, H = dense_context(p, beta, precision, order)
+        step = m.step_joint_async if method == "jmm" else m.step_alternating_async
+        counts = sorted(set(need.values()))
+        ld = torch.zeros(counts[-1], dtype=torch.float64, device="cuda")
+        step(ld[:1], iters=1)          # graph capture and first-launch work outside the timing
+        W.copy_(torch.tensor(p.W0, dtype=W.dtype, device="cuda"))
+        H.copy_(torch.tensor(p.H0, dtype=H.dtype, device="cuda"))
+        stream = torch.cuda.current_stream()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        evs = {c: torch.cuda.Event(enable_timing=True) for c in counts}
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        done = 0
+        for c in counts:
+            for k in range(done, c):
+                step(ld[k:k + 1], iters=1)
+            evs[c].record(stream)
+            done = c
+        torch.cuda.synchronize()
+        out["D_fp64_timed_end"] = fp64_objective(p, beta, W, H)
+        times = {c: ev0.elapsed_time(e) / 1e3 for c, e in evs.items()}
+        m.close()
+    for lb in targets:
+        out[lb] = ({"reached": True, "iters": need[lb], "s": times[need[lb]]} if lb in need
+                   else {"reached": False})
+    return out
+
+
+def time_to_tolerance(p, beta, precision, method, tol, max_iters, order="W"):
+    """The paper's stopping rule (Sec. 4.1.2): iterate until the relative
+    decrease of the objective over one iteration falls to `tol`; wall time
+    including the per-iteration objective read-back the rule needs. The final
+    objective is re-evaluated in FP64."""
+    import torch
+    m, V, W, H = dense_context(p, beta, precision, order)
     step = m.step_joint if method == "jmm" else m.step_alternating
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     prev = step(1)
     it = 1
-    cur = prev
     while it < max_iters:
         cur = step(1)          # objective at the iterate entering this iteration
         it += 1
@@ -319,15 +432,219 @@ def time_to_tolerance(p, beta, precision, method, tol, max_iters, order="W"):
         prev = cur
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    # objective of the returned factors, re-evaluated in FP64 on the GPU
-    m64 = NMF(F, N, K, beta, precision="fp64")
-    V64, W64, H64 = V.double(), W.double(), H.double()
-    m64.set_dense(V64)
-    m64.set_factors(W64, H64)
-    return {"s": el, "iters": it, "D": m64.loss(), "stopped_by_tol": it < max_iters}
+    d = fp64_objective(p, beta, W, H)
+    m.close()
+    return {"precision": precision, "s": el, "iters": it, "D_fp64": d, "stopped_by_tol": it < max_iters}
+
+
+def ttt_block(args, p, beta, precision, order):
+    """Time to the fixed targets D* = D_best x (1 + 1e-4) and x (1 + 1e-3)
+    (D_best: the best long-run FP64-oracle objective, tests/golden/dstar_*.txt)
+    of JMM at the workload's precision, JMM in TF32, BMM in TF32 and BMM in
+    FP64 on the same GPU, every objective evaluated in FP64."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    from make_dstar import read_dstar
+    d = read_dstar(args.workload)
+    if not d or not isinstance(d.get("D_best"), float) or d["D_best"] != d["D_best"]:
+        return {"unavailable": f"no stored D_best for {args.workload}"}
+    best = d["D_best"]
+    targets = {"D*(1e-4)": best * (1 + 1e-4), "D*(1e-3)": best * (1 + 1e-3)}
+    out = {"D_best_oracle": best, "oracle_iterations": d.get("iterations"), "targets": targets}
+    runs = [("jmm_" + precision, precision, "jmm")]
+    if precision != "tf32":
+        runs.append(("jmm_tf32", "tf32", "jmm"))
+    runs += [("bmm_tf32", "tf32", "bmm"), ("bmm_fp64", "fp64", "bmm")]
+    for name, prec, method in runs:
+        out[name] = time_to_target(p, beta, prec, method, order, targets, args.max_ttt_iters)
+    return out
+
+
+def load_peaks():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    if "hbm_gbs" in peaks:
+        return float(peaks["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def timed_steps(step, steps, flush, stream):
+    """Per-step CUDA-event times (ms) of `steps` calls of step(i), the L2
+    flushed between steps outside the events; about 2 ms of untimed flushes
+    are queued first so the host runs ahead of the GPU."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for j in range(30):
+        flush.fill_(float(-j))
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def kernel_pass(m, step, steps, flush):
+    """The library's per-kernel CUDA events (on the launching stream) over
+    `steps` steps: [(kernel, launches, total ms)], launches per step."""
+    import torch
+    m._lib.nmf_reset_timing(m._ctx)
+    m._lib.nmf_set_timing(m._ctx, 1)
+    for i in range(steps):
+        flush.fill_(float(i))
+        step(i)
+    torch.cuda.synchronize()
+    recs, n_launch = timing_records(m)
+    m._lib.nmf_set_timing(m._ctx, 0)
+    return recs, n_launch / max(steps, 1)
+
+
+def roofline_of(rec, recs, F, N, K, esize, order, peak, peak_src, key):
+    name, n, ms = rec
+    per_launch_s = ms / 1e3 / max(n, 1)
+    ab = algorithmic_bytes(name, F, N, K, esize, order)
+    if not ab:
+        return None
+    ach = ab / per_launch_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": NCU_TRAFFIC.get(key + (name,)),
+            "algorithmic_bytes": ab, "avg_launch_us": per_launch_s * 1e6, "launches": n,
+            "peak_source": peak_src, "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
+
+
+def kernel_table(recs, F, N, K, esize, order, peak, peak_src, key):
+    out = {}
+    for r in recs:
+        rf = roofline_of(r, recs, F, N, K, esize, order, peak, peak_src, key)
+        out[r[0]] = {"launches": r[1], "avg_us": round(1e3 * r[2] / max(r[1], 1), 2),
+                     "GB/s": round(rf["achieved"], 1) if rf else None,
+                     "frac": round(rf["frac"], 4) if rf else None}
+    return out
+
+
+def step_roofline(F, N, K, esize, ms_per_step, peak, peak_src):
+    sb = step_bytes(F, N, K, esize)
+    ach = sb / (ms_per_step / 1e3) / 1e9
+    return {"bytes": sb, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": peak_src, "definition": "V read once + both factors read and written once, per iteration"}
+
+
+def dense_extra(p, beta, precision, order, steps, flush, stream, peak, peak_src, name):
+    """iters/s, the step-level and the dominant kernel's HBM fractions of one
+    extra dense workload."""
+    import torch
+    F, N, K = p.shape
+    esize = 8 if precision == "fp64" else 4
+    m, V, W, H = dense_context(p, beta, precision, order)
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    step = lambda i: m.step_joint_async(ld)  # noqa: E731
+    for _ in range(3):
+        step(0)
+    ms = timed_steps(step, steps, flush, stream)
+    per = sum(ms) / len(ms)
+    recs, lps = kernel_pass(m, step, min(steps, 20), flush)
+    dom = max(recs, key=lambda r: r[2]) if recs else None
+    key = (name, precision, order)
+    out = {"workload": WORKLOADS[name]["desc"] if name in WORKLOADS else name, "F": F, "N": N, "K": K, "beta": beta,
+           "precision": precision, "order": order, "iters_per_s": 1e3 / per, "ms_per_step": per,
+           "step_ms_median": statistics.median(ms), "steps": steps,
+           "step_roofline": step_roofline(F, N, K, esize, per, peak, peak_src),
+           "roofline": roofline_of(dom, recs, F, N, K, esize, order, peak, peak_src, key) if dom else None,
+           "kernels": kernel_table(recs, F, N, K, esize, order, peak, peak_src, key),
+           "launches_per_step": lps, "objective": float(ld.item())}
+    m.close()
+    return out
+
+
+def sparse_extra(steps, flush, stream, peak, peak_src):
+    """Sparse KL (Sec. 4.4 stand-in, 20000 x 100000, 0.1 %, K = 50, CSR FP32):
+    nnz/s of JMM and BMM and the HBM fraction against an iteration's
+    algorithmic bytes: the nonzeros' values and column indices once, both
+    factors read and written once (the kernels read the values twice, in
+    the CSR and in the CSC layout, one per half)."""
+    import torch
+    from paper_2106_15214_gb300 import inputs
+    from paper_2106_15214_gb300.binding import NMF
+    p = inputs.sparse_counts()
+    K = p.W0.shape[1]
+    nnz = int(p.val.size)
+    ab = 8 * nnz + 4 * 2 * (p.F + p.N) * K
+    out = {"workload": f"sparse KL (beta=1) F={p.F} N={p.N} nnz={nnz} K={K} CSR fp32", "nnz": nnz,
+           "algorithmic_bytes_per_iter": ab}
+    for method in ("jmm", "bmm"):
+        m = NMF(p.F, p.N, K, 1.0, precision="fp32", order="W")
+        rp = torch.tensor(p.rowptr, dtype=torch.int32, device="cuda")
+        cl = torch.tensor(p.col, dtype=torch.int32, device="cuda")
+        vl = torch.tensor(p.val, dtype=torch.float32, device="cuda")
+        m.set_csr(rp, cl, vl)
+        W = torch.tensor(p.W0, dtype=torch.float32, device="cuda")
+        H = torch.tensor(p.H0, dtype=torch.float32, device="cuda")
+        m.set_factors(W, H)
+        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+        fn = m.step_joint_async if method == "jmm" else m.step_alternating_async
+        step = lambda i: fn(ld)  # noqa: E731
+        for _ in range(3):
+            step(0)
+        ms = timed_steps(step, steps, flush, stream)
+        per = sum(ms) / len(ms)
+        recs, lps = kernel_pass(m, step, min(steps, 10), flush)
+        out[method] = {"ms_per_iter": per, "iters_per_s": 1e3 / per, "nnz_per_s": nnz / (per / 1e3),
+                       "achieved_GBs": ab / (per / 1e3) / 1e9, "frac": ab / (per / 1e3) / 1e9 / peak,
+                       "kernels": {r[0]: {"launches": r[1], "avg_us": round(1e3 * r[2] / max(r[1], 1), 2)}
+                                   for r in recs},
+                       "launches_per_iter": lps, "objective": float(ld.item())}
+        m.close()
+        del rp, cl, vl, W, H
+    out["peak"], out["peak_source"] = peak, peak_src
+    return out
+
+
+def batched_extra(steps, flush, stream, peak, peak_src):
+    """512 batched beta = 1.5 problems (Sec. 4.5 stand-in): time per JMM and
+    per BMM step of the whole batch (one launch per half-sweep over all
+    instances), and the HBM fraction against one read of every V plus the
+    factors read and written once (the floor of a single-read iteration; the
+    batched sweeps read each V once per half)."""
+    import numpy as np
+    import torch
+    from paper_2106_15214_gb300 import inputs
+    from paper_2106_15214_gb300.binding import BatchedNMF
+    probs = inputs.batched_hyperspectral()
+    shapes = [q.shape for q in probs]
+    Vp = torch.tensor(np.concatenate([q.V.ravel() for q in probs]), dtype=torch.float32, device="cuda")
+    Wi = np.concatenate([q.W0.ravel() for q in probs])
+    Hi = np.concatenate([q.H0.ravel() for q in probs])
+    fn_ = sum(F * N for F, N, K in shapes)
+    fk = sum((F + N) * K for F, N, K in shapes)
+    one_read = 4 * fn_ + 8 * fk
+    out = {"workload": f"{len(shapes)} batched beta=1.5 problems, F in [64,256], N in [256,8192], K in [4,32], fp32",
+           "sum_FN": fn_, "bytes_one_read_of_V_plus_factors": one_read}
+    for method in ("jmm", "bmm"):
+        b = BatchedNMF(shapes, 1.5)
+        Wd = torch.tensor(Wi, dtype=torch.float32, device="cuda")
+        Hd = torch.tensor(Hi, dtype=torch.float32, device="cuda")
+        b.set_packed(Vp, Wd, Hd)
+        cap = b.autotune(3)
+        fn = b.step_joint if method == "jmm" else b.step_alternating
+        for _ in range(3):
+            fn(1, want_loss=False)
+        ms = timed_steps(lambda i: fn(1, want_loss=False), steps, flush, stream)
+        per = sum(ms) / len(ms)
+        out[method] = {"ms_per_step": per, "steps_per_s": 1e3 / per, "autotuned_chunk_cap": cap,
+                       "achieved_GBs_one_read": one_read / (per / 1e3) / 1e9,
+                       "frac_one_read": one_read / (per / 1e3) / 1e9 / peak}
+        b.close()
+    out["peak"], out["peak_source"] = peak, peak_src
+    return out
 
 
 def run_ours(args):
+    import gc
+
     import torch
     from paper_2106_15214_gb300 import binding
     from paper_2106_15214_gb300.binding import NMF
@@ -337,15 +654,11 @@ def run_ours(args):
     p, wl = problem(args.workload)
     beta = wl["beta"]
     F, N, K = p.shape
-    precision = args.precision or "tf32"
+    precision = args.precision or wl["precision"]
+    order = args.order or wl["order"]
     esize = 8 if precision == "fp64" else 4
     dt = torch.float64 if precision == "fp64" else torch.float32
-    m = NMF(F, N, K, beta, precision=precision, order=args.order)
-    V = torch.tensor(p.V, dtype=dt, device="cuda")
-    W = torch.tensor(p.W0, dtype=dt, device="cuda")
-    H = torch.tensor(p.H0, dtype=dt, device="cuda")
-    m.set_dense(V)
-    m.set_factors(W, H)
+    m, V, W, H = dense_context(p, beta, precision, order)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     loss_dev = torch.zeros(max(args.steps, args.warmup, 1), dtype=torch.float64, device="cuda")
@@ -360,7 +673,6 @@ def run_ours(args):
     # of untimed flushes are queued first so the host runs ahead of the GPU
     # and a host-side pause cannot leave the GPU idle inside a step's events.
     # The clock sampler is started (and has delivered a sample) before it.
-    import gc
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
@@ -383,61 +695,30 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"device status {st} after the timed region")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_s = sum(step_ms) / 1e3
-    dev_s_max = reduce_max(dev_s, world)
+    dev_s_max = reduce_max(sum(step_ms) / 1e3, world)
     value = aggregate_rate(world, args.steps, dev_s_max)
     losses = loss_dev[:args.steps].cpu().tolist()
+    ms_per_step = 1e3 * dev_s_max / args.steps
+    peak, peak_src = load_peaks()
+    key = (args.workload, precision, order)
     # Kernel pass: the same steps with the library's per-kernel CUDA events on
     # the launching stream (they add a little time per launch, so the value
     # above comes from the untimed pass): per-kernel durations, launch counts.
-    kt_steps = 0 if args.no_kernel_timing else min(args.steps, 50)
     recs, launches_per_step = [], None
-    if kt_steps:
-        m._lib.nmf_reset_timing(m._ctx)
-        m._lib.nmf_set_timing(m._ctx, 1)
-        for i in range(kt_steps):
-            flush.fill_(float(i))
-            m.step_joint_async(loss_dev[i:i + 1])
-        torch.cuda.synchronize()
-        recs, n_launch = timing_records(m)
-        m._lib.nmf_set_timing(m._ctx, 0)
-        launches_per_step = n_launch / kt_steps
-    # dominant kernel of the step and its roofline
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
-    def roof_of(rec):
-        name, n, ms = rec
-        per_launch_s = ms / 1e3 / max(n, 1)
-        ab = algorithmic_bytes(name, F, N, K, esize)
-        if not ab:
-            return None
-        ach = ab / per_launch_s / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": NCU_TRAFFIC.get((args.workload, precision, args.order, name)),
-                "algorithmic_bytes": ab,
-                "avg_launch_us": per_launch_s * 1e6, "launches": n, "peak_source": peak_src,
-                "share_of_step": ms / (sum(r[2] for r in recs) or 1.0)}
-
+    if not args.no_kernel_timing:
+        recs, launches_per_step = kernel_pass(m, lambda i: m.step_joint_async(loss_dev[i:i + 1]),
+                                              min(args.steps, 50), flush)
     dom = max(recs, key=lambda r: r[2]) if recs else None
-    roof = roof_of(dom) if dom else None
-    kernels = {}
-    for r in recs:
-        rf = roof_of(r)
-        kernels[r[0]] = {"launches": r[1], "avg_us": round(1e3 * r[2] / max(r[1], 1), 2),
-                         "GB/s": round(rf["achieved"], 1) if rf else None,
-                         "frac": round(rf["frac"], 4) if rf else None}
+    roof = roofline_of(dom, recs, F, N, K, esize, order, peak, peak_src, key) if dom else None
+    kernels = kernel_table(recs, F, N, K, esize, order, peak, peak_src, key)
     launches = round(launches_per_step * args.steps) if launches_per_step is not None else None
+    m.close()
+    del V, W, H
     # end to end through the host-buffer C-ABI call
     Vh = torch.tensor(p.V, dtype=dt).pin_memory()
     Wh = torch.tensor(p.W0, dtype=dt).pin_memory()
     Hh = torch.tensor(p.H0, dtype=dt).pin_memory()
-    me = NMF(F, N, K, beta, precision=precision, order=args.order)
+    me = NMF(F, N, K, beta, precision=precision, order=order)
     for _ in range(3):
         me.step_joint_host(Vh, Wh, Hh, 1)
     torch.cuda.synchronize()
@@ -446,40 +727,52 @@ def run_ours(args):
     for _ in range(e2e_steps):
         me.step_joint_host(Vh, Wh, Hh, 1)
     e2e_s = reduce_max(time.perf_counter() - t0, world)
+    me.close()
     e2e = {"value": world * e2e_steps / e2e_s, "unit": "iters/s",
            "h2d_bytes_per_step": (F * N + F * K + K * N) * esize,
            "d2h_bytes_per_step": (F * K + K * N) * esize + 8}
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[precision],
         "data": "synthetic",
         "config": {"workload": wl["desc"], "F": F, "N": N, "K": K, "beta": beta, "precision": precision,
-                   "order": args.order, "step": "one JMM outer iteration (L=1) with objective and normalisation",
+                   "order": order, "step": "one JMM outer iteration (L=1) with objective and normalisation",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roof, "gpu_launches": launches, "kernels": kernels,
-        "e2e": e2e, "wall_s": wall,
+        "roofline": roof, "step_roofline": step_roofline(F, N, K, esize, ms_per_step, peak, peak_src),
+        "gpu_launches": launches, "kernels": kernels, "e2e": e2e, "wall_s": wall,
         "step_ms_median": statistics.median(step_ms),
         "objective": {"first": losses[0], "last": losses[-1]},
     }
     if rank == 0:
         if not args.no_cpu_baseline:
-            n_it, el = time_oracle(p, beta, args.cpu_seconds)
+            n_it, el = time_oracle(p, beta, args.cpu_seconds, order=order)
             line["cpu_baseline"] = {"value": n_it / el, "unit": "iters/s", "cores": cpu_threads(), "kind": "oracle",
                                     "sample": f"{n_it} full JMM iterations of the workload ({el:.1f} s, numpy FP64)"}
         if not args.no_ttt:
+            line["time_to_target"] = ttt_block(args, p, beta, precision, order)
             tol = 1e-5
             line["time_to_tolerance"] = {
-                "tol": tol, "rule": "(D_prev - D)/D <= tol, max %d iterations" % args.max_ttt_iters,
-                "jmm": time_to_tolerance(p, beta, precision, "jmm", tol, args.max_ttt_iters, args.order),
-                "bmm_same_precision": time_to_tolerance(p, beta, precision, "bmm", tol,
-                                                        args.max_ttt_iters, args.order),
-                "bmm_fp64": time_to_tolerance(p, beta, "fp64", "bmm", tol, args.max_ttt_iters, args.order),
+                "tol": tol, "rule": "(D_prev - D)/D <= tol (Sec. 4.1.2), max %d iterations" % args.max_ttt_iters,
+                "jmm": time_to_tolerance(p, beta, precision, "jmm", tol, args.max_ttt_iters, order),
+                "bmm_tf32": time_to_tolerance(p, beta, "tf32", "bmm", tol, args.max_ttt_iters, order),
+                "bmm_fp64": time_to_tolerance(p, beta, "fp64", "bmm", tol, args.max_ttt_iters, order),
             }
-    clocks = clk.summary()
-    line["clocks"] = clocks
+        if not args.no_extras:
+            extras = {}
+            if args.workload == "spectrogram":
+                extras["tf32_two_sweeps"] = dense_extra(p, beta, "tf32", "W", 200, flush, stream, peak, peak_src,
+                                                        "spectrogram")
+                big, _ = problem("spectrogram_large")
+                extras["spectrogram_large"] = dense_extra(big, beta, precision, order, 100, flush, stream, peak,
+                                                          peak_src, "spectrogram_large")
+                del big
+            extras["sparse_kl"] = sparse_extra(20, flush, stream, peak, peak_src)
+            extras["batched"] = batched_extra(20, flush, stream, peak, peak_src)
+            line["extras"] = extras
+    line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -757,7 +757,13 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  // No programmatic dependent launch by default: launched early, the clusters
+  // are placed around the previous kernel's blocks, and (measured on GB300) in
+  // most steps one of the co-resident clusters the grid is sized for was left
+  // for a second wave, nearly doubling the kernel's time. NMF_FU_PDL=1 turns
+  // it on (A/B measurement).
+  static const bool pdl = std::getenv("NMF_FU_PDL") && std::atoi(std::getenv("NMF_FU_PDL")) == 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   cudaError_t e = cudaSuccess;
 #define NMF_FU_CASE(BKV)                                                                   \
   case BKV:                                                                                \

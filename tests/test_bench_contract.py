@@ -22,19 +22,25 @@ def test_reference_arm_prints_one_contract_line():
     assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["vs_baseline"] is None and d["dtype"] == "f64" and d["data"] == "synthetic"
-    assert "faces" in d["config"]["workload"]
+    assert "Itakura-Saito" in d["config"]["workload"] and d["config"]["N"] == 20000
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 def test_algorithmic_bytes():
-    F, N, K, s = 361, 2429, 49, 4
+    """V once, each distinct factor-sized operand once (no tensor-core copies),
+    outputs once; the fused sweep reads V once per iteration."""
+    F, N, K, s = 513, 20000, 20, 4
     V, FK, KN = F * N * s, F * K * s, K * N * s
-    assert bench.algorithmic_bytes("tc_row_sweep", F, N, K) == V + FK + 3 * KN + 2 * FK
-    assert bench.algorithmic_bytes("tc_col_sweep", F, N, K) == V + 3 * FK + KN + 2 * KN
-    assert bench.algorithmic_bytes("cols_epilogue", F, N, K) == 7 * KN + 5 * FK
+    assert bench.algorithmic_bytes("tc_row_sweep", F, N, K, order="W") == V + FK + KN + 2 * FK
+    assert bench.algorithmic_bytes("tc_col_sweep", F, N, K, order="W") == V + 3 * FK + KN + 2 * KN
+    assert bench.algorithmic_bytes("tc_col_sweep", F, N, K, order="H") == V + FK + KN + 2 * KN
+    assert bench.algorithmic_bytes("tc_row_sweep", F, N, K, order="H") == V + 3 * KN + FK + 2 * FK
+    assert bench.algorithmic_bytes("tc_fused", F, N, K, order="H") == V + 3 * FK + 2 * KN
+    assert bench.algorithmic_bytes("cols_epilogue", F, N, K) == 4 * KN + 3 * FK
     assert bench.algorithmic_bytes("nope", F, N, K) is None
+    assert bench.step_bytes(F, N, K) == V + 2 * (FK + KN)
 
 
 def test_clock_sampler_keeps_samples_inside_the_timed_region():
