@@ -640,18 +640,24 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
       return NMF_OK;
     }
   }
-  // NMF_BF16: the fused single-read H-first iteration (tc_fused.cu): copies
-  // of W~, H~ | the fused sweep (product, A, B, objective, H update, both
-  // contractions; H written) | W update from its partial slices (column norms
-  // and the objective finalised by its last block) | normalisation.
+  // NMF_BF16: the fused single-read H-first iteration (tc_fused.cu): the
+  // fused sweep (product, A, B, objective, H update, both contractions; H
+  // written) | W update from its partial slices (column norms and the
+  // objective finalised by its last block) | normalisation fused with the
+  // next iteration's copies of W~, H~. The copies of the first iteration come
+  // from the previous call's last kernel while nothing changed W and H in
+  // between (copiesValid), else from the copies kernel.
   if constexpr (std::is_same<T, float>::value) {
     if (c->prec == NMF_BF16) {
       const Prob<float>& P0 = c->hpf[0];
       const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
+      const bool haveCopies = c->copiesValid;
+      c->copiesValid = false;
       for (int it = 0; it < iters; ++it) {
         const bool lossHere = wantLoss && it == iters - 1;
-        NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
-                     [&] { return launch_tc_copies<float>(P0, true, true, true, status, st); }));
+        if (it == 0 && !haveCopies)
+          NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
+                       [&] { return launch_tc_copies<float>(P0, true, true, true, status, st); }));
         NMF_CU(timed(&c->timer, st, "tc_fused", 1, [&] {
           return launch_tc_fused(P0, c->tcmaps, bp, ncl, lp, status, c->waitLimitNs, c->extraArrivals, st);
         }));
@@ -665,11 +671,10 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] {
           return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 0, bp, nullptr, status, st, 3, f);
         }));
-        if (norm)
-          NMF_CU(timed(&c->timer, st, "normalize", 1, [&] { return launch_normalize_apply<T>(pl, status, st); }));
+        NMF_CU(timed(&c->timer, st, "normalize_next", 1, [&] { return launch_fused_next<float>(P0, norm, status, st); }));
       }
       c->lossFused = true;
-      c->copiesValid = false;
+      c->copiesValid = true;
       return NMF_OK;
     }
   }

@@ -201,6 +201,12 @@ inline int rows_epilogue_lanes(const Plan<T>& pl, int tc) {
 // `tilde` the W~, H~ copies too (the begin of a tensor-core iteration).
 template <typename T>
 cudaError_t launch_tc_copies(const Prob<T>& P, bool doW, bool doH, bool tilde, const int* status, cudaStream_t st);
+// The last kernel of a fused single-read iteration: W /= norms, H *= norms
+// (norm; Sec. 4.1.2) written back, and the copies the next iteration's fused
+// sweep reads (W~, H~ and their TF32 shadows sWS, sHT) made from the result.
+constexpr int COPIES_APPLY = 1, COPIES_LEAN = 2;
+template <typename T>
+cudaError_t launch_fused_next(const Prob<T>& P, bool norm, const int* status, cudaStream_t st);
 // The last H epilogue of a W-first tensor-core iteration (normalisation on)
 // fused with the next iteration's copies (what launch_tc_copies with tilde
 // would make from the final W, H); single problem.

@@ -875,9 +875,12 @@ shadow_factors_kernel(Prob<T> P, int which, const int* __restrict__ status) {
 // [32 b, 32 b + 32) of H, all K rows: read along n, H~ and sHS (K x Np) written
 // along n, sHT (N x ks) written along k after a transpose in shared memory
 // (a direct transposed store would put every element in its own sector).
+// mode (the fused single-read path's last kernel, COPIES_*): APPLY scales W's
+// columns down and H's rows up by P.norms (Sec. 4.1.2) and writes W and H
+// back before copying; LEAN skips the copies that path does not read (sWT, sHS).
 template <typename T>
 __global__ void __launch_bounds__(EW)
-tc_copies_kernel(Prob<T> P, int wBlocks, int doW, int doH, int tilde, const int* __restrict__ status) {
+tc_copies_kernel(Prob<T> P, int wBlocks, int doW, int doH, int tilde, const int* __restrict__ status, int mode) {
   pdl_trigger();
   pdl_wait();
   if (*status) return;
@@ -886,12 +889,17 @@ tc_copies_kernel(Prob<T> P, int wBlocks, int doW, int doH, int tilde, const int*
     if (!doW) return;
     const int64_t idx = (int64_t)blockIdx.x * EW + threadIdx.x;
     if (idx < P.F * P.K) {
-      const T w = P.W[idx];
-      if (tilde) P.Wt[idx] = w;
+      T w = P.W[idx];
       const int64_t f = idx / P.K, k = idx - f * P.K;
+      if (mode & COPIES_APPLY) {
+        const T nk = P.norms[k];
+        if (nk > T(0)) w = w / nk;
+        P.W[idx] = w;
+      }
+      if (tilde) P.Wt[idx] = w;
       const float r = tf32_round((float)w);
       P.sWS[f * P.ks + k] = (T)r;
-      P.sWT[k * P.Fp + f] = (T)r;
+      if (!(mode & COPIES_LEAN)) P.sWT[k * P.Fp + f] = (T)r;
     }
     return;
   }
@@ -901,10 +909,15 @@ tc_copies_kernel(Prob<T> P, int wBlocks, int doW, int doH, int tilde, const int*
   const int64_t n = n0 + lane;
   for (int k = w; k < P.K; k += EW / 32) {
     if (n < P.N) {
-      const T h = P.H[(int64_t)k * P.N + n];
+      T h = P.H[(int64_t)k * P.N + n];
+      if (mode & COPIES_APPLY) {
+        const T nk = P.norms[k];
+        if (nk > T(0)) h = h * nk;
+        P.H[(int64_t)k * P.N + n] = h;
+      }
       if (tilde) P.Ht[(int64_t)k * P.N + n] = h;
       const float r = tf32_round((float)h);
-      P.sHS[(int64_t)k * P.Np + n] = (T)r;
+      if (!(mode & COPIES_LEAN)) P.sHS[(int64_t)k * P.Np + n] = (T)r;
       tile[lane][k] = r;
     }
   }
@@ -921,7 +934,15 @@ cudaError_t launch_tc_copies(const Prob<T>& P, bool doW, bool doH, bool tilde, c
   const int hBlocks = doH ? (int)((P.N + 31) / 32) : 0;
   if (wBlocks + hBlocks == 0) return cudaSuccess;
   return launch_pdl(tc_copies_kernel<T>, dim3(wBlocks + hBlocks), dim3(EW), 0, st, P, wBlocks, doW ? 1 : 0, doH ? 1 : 0,
-                    tilde ? 1 : 0, status);
+                    tilde ? 1 : 0, status, 0);
+}
+
+template <typename T>
+cudaError_t launch_fused_next(const Prob<T>& P, bool norm, const int* status, cudaStream_t st) {
+  const int wBlocks = (int)((P.F * P.K + EW - 1) / EW);
+  const int hBlocks = (int)((P.N + 31) / 32);
+  return launch_pdl(tc_copies_kernel<T>, dim3(wBlocks + hBlocks), dim3(EW), 0, st, P, wBlocks, 1, 1, 1, status,
+                    COPIES_LEAN | (norm ? COPIES_APPLY : 0));
 }
 
 template <typename T>
@@ -1183,6 +1204,7 @@ cudaError_t launch_kkt(const T* W, const T* gW, int64_t nW, const T* H, const T*
   template cudaError_t launch_begin_iteration<T>(const Plan<T>&, const int*, cudaStream_t);        \
   template cudaError_t launch_normalize_parts<T>(const Plan<T>&, const T*, int, const int*, cudaStream_t); \
   template cudaError_t launch_tc_copies<T>(const Prob<T>&, bool, bool, bool, const int*, cudaStream_t); \
+  template cudaError_t launch_fused_next<T>(const Prob<T>&, bool, const int*, cudaStream_t);       \
   template cudaError_t launch_cols_next<T>(const Plan<T>&, const Prob<T>&, const BetaParams&, int*, cudaStream_t); \
   template cudaError_t launch_normalize<T>(const Plan<T>&, const int*, cudaStream_t);              \
   template cudaError_t launch_kkt<T>(const T*, const T*, int64_t, const T*, const T*, int64_t,     \

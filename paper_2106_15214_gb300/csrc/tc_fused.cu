@@ -65,12 +65,14 @@ constexpr int FU_MAXV = 6;
 constexpr int FU_ETIMEOUT = 5;
 constexpr uint32_t FU_TB = 16384;    // one V tile (128 x 32 floats) or one H~^T batch (128 x 32)
 constexpr size_t FU_SMEM_LIMIT = 227 * 1024;
-// TMEM columns: batch buffers 0 and 1 (Vt of 4 tiles, then [A | B] bf16 in
-// place), H-accumulator slots (Hn at +0, Hd at +32), P, Q, W~ rows (MMA1 A).
-constexpr uint32_t FT_BUF = 0, FT_HACC = 256, FT_P = 384, FT_Q = 416, FT_W = 448, FT_COLS = 512;
+// TMEM columns: three batch buffers (Vt of 4 tiles, then [A | B] bf16 in
+// place), the H accumulator (Hn at +0, Hd at +32), P, Q.
+constexpr int FU_NBUF = 3;
+constexpr uint32_t FT_BUF = 0, FT_HACC = 384, FT_P = 448, FT_Q = 480, FT_COLS = 512;
 
 struct FuLayout {
   uint32_t fa0;      // 2 H~^T batch slots (128 rows x 32 floats, SW128)
+  uint32_t wt;       // W~ rows (MMA1's A operand, 128 rows x 32 floats, SW128)
   uint32_t v0;       // nv V tiles
   uint32_t sa, sb;   // A^T, B^T copies: 2 K-atoms (64 rows f each) x 128 rows n x 128 B (bf16, SW128)
   uint32_t wb;       // W~^T bf16: 2 K-atoms x kp rows x 128 B
@@ -84,7 +86,8 @@ struct FuLayout {
 __host__ __device__ inline FuLayout fu_layout(int K, int kp, int nv) {
   FuLayout L;
   L.fa0 = 0;
-  L.v0 = 2 * FU_TB;
+  L.wt = 2 * FU_TB;
+  L.v0 = 3 * FU_TB;
   L.sa = L.v0 + (uint32_t)nv * FU_TB;
   L.sb = L.sa + 32768u;
   L.wb = L.sb + 32768u;
@@ -105,8 +108,8 @@ inline int fu_pick_nv(int K, int kp) {
 
 struct FuBars {
   uint64_t vfull[FU_MAXV], vempty[FU_MAXV];
-  uint64_t fafull[2], fafree[2], tfull[2], buffree[2], haccfull[2], haccfree[2], chiready[2];
-  uint64_t stashfull, stashfree, once, onceT, done;
+  uint64_t fafull[2], fafree[2], tfull[FU_NBUF], buffree[FU_NBUF], chiready[2];
+  uint64_t haccfull, haccfree, stashfull, stashfree, once, done;
   // arrived on by every block of the cluster, alternating by batch parity: a
   // block can arrive for batch j + 1 before another block's arrival for batch
   // j has landed (that one reaches the barrier only through a third block),
@@ -171,13 +174,15 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned 
     mbar_init(&B.vfull[s], 1u);
     mbar_init(&B.vempty[s], 8u);           // the 8 warps of the group reading the tile
   }
+  for (int s = 0; s < FU_NBUF; ++s) {
+    mbar_init(&B.tfull[s], 1u);
+    mbar_init(&B.buffree[s], 1u);
+  }
+  mbar_init(&B.haccfull, 1u);
+  mbar_init(&B.haccfree, 4u);              // the 4 exchange warps
   for (int s = 0; s < 2; ++s) {
     mbar_init(&B.fafull[s], 1u);
     mbar_init(&B.fafree[s], 1u);
-    mbar_init(&B.tfull[s], 1u);
-    mbar_init(&B.buffree[s], 1u);
-    mbar_init(&B.haccfull[s], 1u);
-    mbar_init(&B.haccfree[s], 4u);         // the 4 exchange warps
     mbar_init(&B.chiready[s], 4u);
     mbar_init(&B.mailfull[s], 4u * (uint32_t)c + extra);    // every exchange warp of every block
     mbar_init(&B.chifull[s], 4u * (uint32_t)c + extra);
@@ -185,7 +190,6 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned 
   mbar_init(&B.stashfull, 32u);            // 4 tiles x 8 warps per batch
   mbar_init(&B.stashfree, 1u);
   mbar_init(&B.once, 1u);
-  mbar_init(&B.onceT, 4u);
   mbar_init(&B.done, 1u);
   fence_mbar_init();
 }
@@ -270,7 +274,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
     // ---------------- operand loads ----------------
     if (nbr > 0 && elect_one()) {
       mbar_arrive_expect_tx(&bars.once, FU_TB);
-      tma_load_2d(base + L.sa, &tmW, 0, (int)m0, &bars.once);          // W~ rows (staging over the A^T copy)
+      tma_load_2d(base + L.wt, &tmW, 0, (int)m0, &bars.once);          // W~ rows (TF32 copy)
     }
     __syncwarp();
     int issued = 0;
@@ -313,46 +317,46 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
         mbar_wait(&bars.vfull[t % nv], (uint32_t)(t / nv) & 1u, 100000000ull);
   } else if (warp == 2) {
     // ---------------- MMA issue ----------------
-    // MMA1(j): Vt of batch j into buffer j & 1. H-MMA(j): the A^T, B^T copies
-    // times W~ into H-accumulator slot j & 1. W-MMA(j): [A | B] of buffer
-    // j & 1 times chi slot j & 1 into P, Q. Order: MMA1(0), MMA1(1), then per
-    // j: H-MMA(j) (as soon as the epilogue has finished batch j, so that the
-    // exchange of batch j starts at once), W-MMA(j - 1), MMA1(j + 1) (its
-    // buffer is the one W-MMA(j - 1) read); finally W-MMA(last). The exchange
-    // of batch j thus runs while the epilogue works on batch j + 1.
+    // MMA1(j): Vt of batch j (W~ rows and the H~^T slot j & 1, both in shared
+    // memory) into buffer j % 3. H-MMA(j): the A^T, B^T copies times W~ into
+    // the H accumulator. W-MMA(j): [A | B] of buffer j % 3 times chi slot
+    // j & 1 into P, Q. Order: MMA1(0..2), then per j: H-MMA(j) (as soon as
+    // the epilogue has finished batch j, so that the exchange of batch j
+    // starts at once), W-MMA(j - 1), MMA1(j + 2) (its buffer is the one
+    // W-MMA(j - 1) read); finally W-MMA(last). The exchange of batch j thus
+    // has the epilogue of batches j + 1 and j + 2 to complete in: the three
+    // buffers take it off the per-batch critical path.
     const uint32_t id1 = idesc(128, 128, kFmtTF32), idk = idesc(128, kp, kFmtBF16);
-    const uint64_t dFa = desc_sw128(smem_u32(base + L.fa0));
+    const uint64_t dFa = desc_sw128(smem_u32(base + L.fa0)), dWt = desc_sw128(smem_u32(base + L.wt));
     const uint64_t dSA = desc_sw128(smem_u32(base + L.sa)), dSB = desc_sw128(smem_u32(base + L.sb));
     const uint64_t dWb = desc_sw128(smem_u32(base + L.wb)), dChi = desc_sw128(smem_u32(base + L.chi0));
     const uint32_t atomK16 = (uint32_t)(kp * 128) >> 4;   // one K-atom of kp rows, in 16-byte units
-    bool ok = nbr > 0 && __all_sync(0xffffffffu, fu_wait(&bars.onceT, 0u, &s_abort, S.status, lim));
+    bool ok = nbr > 0 && __all_sync(0xffffffffu, fu_wait(&bars.once, 0u, &s_abort, S.status, lim));
     auto mma1 = [&](int j) -> bool {
-      const int s = j & 1;
+      const int s = j & 1, b = j % FU_NBUF;
       if (!__all_sync(0xffffffffu, fu_wait(&bars.fafull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim)))
         return false;
-      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.buffree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
-                                                       S.status, lim)))
+      if (j >= FU_NBUF && !__all_sync(0xffffffffu, fu_wait(&bars.buffree[b], (uint32_t)(j / FU_NBUF - 1) & 1u,
+                                                             &s_abort, S.status, lim)))
         return false;
       fence_after_sync();
       if (elect_one()) {
         for (int ks = 0; ks < kp / 8; ++ks)
-          mma_tf32_ts(tbase + FT_BUF + 128u * s, tbase + FT_W + 8u * ks, dFa + (uint64_t)(s * (FU_TB >> 4)) + 2u * ks,
-                      id1, ks > 0);
-        mma_commit(&bars.tfull[s]);
+          mma_tf32(tbase + FT_BUF + 128u * b, dWt + 2u * ks, dFa + (uint64_t)(s * (FU_TB >> 4)) + 2u * ks, id1, ks > 0);
+        mma_commit(&bars.tfull[b]);
         mma_commit(&bars.fafree[s]);
       }
       __syncwarp();
       return true;
     };
     auto hmma = [&](int j) -> bool {
-      const int s = j & 1;
       if (!__all_sync(0xffffffffu, fu_wait(&bars.stashfull, (uint32_t)j & 1u, &s_abort, S.status, lim))) return false;
-      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.haccfree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
-                                                       S.status, lim)))
+      // the exchange has read batch j - 1 out of the accumulator
+      if (j >= 1 && !__all_sync(0xffffffffu, fu_wait(&bars.haccfree, (uint32_t)(j - 1) & 1u, &s_abort, S.status, lim)))
         return false;
       fence_after_sync();
       if (elect_one()) {
-        const uint32_t acc = tbase + FT_HACC + 64u * s;
+        const uint32_t acc = tbase + FT_HACC;
         for (int st = 0; st < 8; ++st) {               // K = 128 rows f in steps of 16
           const uint64_t ka = 1024u * (st >> 2) + 2u * (st & 3);
           const uint64_t kb = (uint64_t)atomK16 * (st >> 2) + 2u * (st & 3);
@@ -360,18 +364,18 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
           mma_bf16(acc + 32u, dSB + ka, dWb + kb, idk, st > 0);
         }
         mma_commit(&bars.stashfree);
-        mma_commit(&bars.haccfull[s]);
+        mma_commit(&bars.haccfull);
       }
       __syncwarp();
       return true;
     };
     auto wmma = [&](int j) -> bool {
-      const int s = j & 1;
+      const int s = j & 1, b = j % FU_NBUF;
       if (!__all_sync(0xffffffffu, fu_wait(&bars.chiready[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim)))
         return false;
       fence_after_sync();
       if (elect_one()) {
-        const uint32_t buf = tbase + FT_BUF + 128u * s;
+        const uint32_t buf = tbase + FT_BUF + 128u * b;
         const uint64_t c1 = dChi + (uint64_t)(s * (L.chiSlot >> 4)), c2 = c1 + 2u * atomK16;
         for (int st = 0; st < 8; ++st) {               // K = 128 columns n in steps of 16
           const uint32_t a = buf + 32u * (st >> 1) + 16u * (st & 1);
@@ -380,17 +384,16 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
           mma_bf16_ts(tbase + FT_P, a, c1 + kb, idk, acc);
           mma_bf16_ts(tbase + FT_Q, a + 8u, c2 + kb, idk, acc);
         }
-        mma_commit(&bars.buffree[s]);
+        mma_commit(&bars.buffree[b]);
       }
       __syncwarp();
       return true;
     };
-    if (ok) ok = mma1(0);
-    if (ok && nbr > 1) ok = mma1(1);
+    for (int j = 0; ok && j < nbr && j < FU_NBUF; ++j) ok = mma1(j);
     for (int j = 0; ok && j < nbr; ++j) {
       ok = hmma(j);
       if (ok && j >= 1) ok = wmma(j - 1);
-      if (ok && j >= 1 && j + 1 < nbr) ok = mma1(j + 1);
+      if (ok && j >= 1 && j + FU_NBUF - 1 < nbr) ok = mma1(j + FU_NBUF - 1);
     }
     if (ok && nbr > 0) wmma(nbr - 1);
     if (elect_one()) mma_commit(&bars.done);
@@ -408,28 +411,10 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
     // this thread's place in the transposed copies: K-atom mrow / 64, element mrow % 64 (pairs: even element)
     const uint32_t atomOff = (uint32_t)(mrow >> 6) * 16384u, ePair = (uint32_t)(mrow & 62);
     const bool odd = lane & 1;
-    if (ew < 4 && nbr > 0) {
-      // warps 4-7 move the W~ rows (MMA1's A operand, kp columns) from shared memory to TMEM
-      if (__all_sync(0xffffffffu, fu_wait(&bars.once, 0u, &s_abort, S.status, lim))) {
-        for (int k0 = 0; k0 < kp; k0 += 16) {
-          float o[16];
-          #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float4 v4 = *reinterpret_cast<const float4*>(base + L.sa + sw128_offset(mrow, 4 * k0 + 16 * i));
-            o[4 * i] = v4.x; o[4 * i + 1] = v4.y; o[4 * i + 2] = v4.z; o[4 * i + 3] = v4.w;
-          }
-          tmem_st16(tbase + FT_W + lane_off + k0, o);
-        }
-        tmem_st_wait();
-        fence_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars.onceT);
-      }
-    }
     for (int t = g; t < 4 * nbr; t += 2) {
-      const int j = t >> 2, q = t & 3, s = j & 1;
+      const int j = t >> 2, q = t & 3, b = j % FU_NBUF;
       const int sv = t % nv;
-      const uint32_t col = FT_BUF + 128u * s + 32u * q + jb0;
+      const uint32_t col = FT_BUF + 128u * b + 32u * q + jb0;
       // A group starts a new batch only once the previous batch's H contraction
       // has completed. It then also may overwrite the transposed copies; and on
       // GB300 a first tile whose TMEM reads and writes overlapped that
@@ -438,7 +423,8 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
       if (q == g && j >= 1 &&
           !__all_sync(0xffffffffu, fu_wait(&bars.stashfree, (uint32_t)(j - 1) & 1u, &s_abort, S.status, lim)))
         break;
-      if (!__all_sync(0xffffffffu, fu_wait(&bars.tfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim))) break;
+      if (!__all_sync(0xffffffffu, fu_wait(&bars.tfull[b], (uint32_t)(j / FU_NBUF) & 1u, &s_abort, S.status, lim)))
+        break;
       if (!__all_sync(0xffffffffu, fu_wait(&bars.vfull[sv], (uint32_t)(t / nv) & 1u, &s_abort, S.status, lim))) break;
       fence_after_sync();
       float vt[16], vv[16];
@@ -516,13 +502,13 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
       // handshake of batch j completes: each block writes its mailbox after
       // its H contraction of batch j, whose completion covers its W
       // contraction of batch j - 2. So two handshakes per batch suffice.
-      bool go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim));
+      bool go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull, (uint32_t)j & 1u, &s_abort, S.status, lim));
       if (go) {
         fence_after_sync();
         for (int k0 = 0; k0 < kp; k0 += 16) {
           float hn[16], hd[16];
-          tmem_ld16(tbase + FT_HACC + 64u * s + lane_off + k0, hn);
-          tmem_ld16(tbase + FT_HACC + 64u * s + 32u + lane_off + k0, hd);
+          tmem_ld16(tbase + FT_HACC + lane_off + k0, hn);
+          tmem_ld16(tbase + FT_HACC + 32u + lane_off + k0, hd);
           tmem_ld_wait();
           #pragma unroll
           for (int i = 0; i < 16; ++i)
@@ -533,7 +519,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
         }
         fence_before_sync();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bars.haccfree[s]);
+        if (lane == 0) mbar_arrive(&bars.haccfree);
         // each warp publishes its own columns: warp barrier (cumulative), one
         // fence at cluster scope, relaxed arrivals
         __syncwarp();
