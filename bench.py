@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--max-ttt-iters", type=int, default=6000)
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="skip the per-kernel timing pass (no roofline, no launch count)")
+    ap.add_argument("--extra", default=None, choices=["sparse_kl", "batched"],
+                    help="run only this extra workload (--steps timed steps) and print its JSON object")
     return ap.parse_args()
 
 
@@ -246,6 +248,8 @@ def algorithmic_bytes(kernel, F, N, K, esize=4, order="W"):
         # W, H in; W~, H~ out
         "begin_iteration": 2 * (FK + KN),
         "normalize": 2 * (FK + KN),
+        # W, H in; W, H (normalised) out; the next iteration's W~, H~ are the same values
+        "normalize_next": 2 * (FK + KN),
     }
     return table.get(kernel)
 
@@ -622,20 +626,23 @@ def batched_extra(steps, flush, stream, peak, peak_src):
     fn_ = sum(F * N for F, N, K in shapes)
     fk = sum((F + N) * K for F, N, K in shapes)
     one_read = 4 * fn_ + 8 * fk
-    out = {"workload": f"{len(shapes)} batched beta=1.5 problems, F in [64,256], N in [256,8192], K in [4,32], fp32",
+    out = {"workload": f"{len(shapes)} batched beta=1.5 problems, F in [64,256], N in [256,8192], K in [4,32]",
            "sum_FN": fn_, "bytes_one_read_of_V_plus_factors": one_read}
-    for method in ("jmm", "bmm"):
-        b = BatchedNMF(shapes, 1.5)
+    # JMM on the fused single-read path (one launch over all problems' work
+    # items; bf16 contractions, H first), then JMM and BMM on the FP32 SIMT sweeps
+    for method, prec, order in (("jmm_bf16", "bf16", "H"), ("jmm", "fp32", "W"), ("bmm", "fp32", "W")):
+        b = BatchedNMF(shapes, 1.5, precision=prec, order=order)
         Wd = torch.tensor(Wi, dtype=torch.float32, device="cuda")
         Hd = torch.tensor(Hi, dtype=torch.float32, device="cuda")
         b.set_packed(Vp, Wd, Hd)
         cap = b.autotune(3)
-        fn = b.step_joint if method == "jmm" else b.step_alternating
+        fn = b.step_alternating if method == "bmm" else b.step_joint
         for _ in range(3):
             fn(1, want_loss=False)
         ms = timed_steps(lambda i: fn(1, want_loss=False), steps, flush, stream)
         per = sum(ms) / len(ms)
-        out[method] = {"ms_per_step": per, "steps_per_s": 1e3 / per, "autotuned_chunk_cap": cap,
+        out[method] = {"precision": prec, "order": order, "ms_per_step": per, "steps_per_s": 1e3 / per,
+                       "autotuned_chunk_cap": cap,
                        "achieved_GBs_one_read": one_read / (per / 1e3) / 1e9,
                        "frac_one_read": one_read / (per / 1e3) / 1e9 / peak}
         b.close()
@@ -782,10 +789,23 @@ def run_ours(args):
     return 0
 
 
+def run_extra(args):
+    import torch
+    from paper_2106_15214_gb300 import binding
+    binding.load()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peak, peak_src = load_peaks()
+    fn = sparse_extra if args.extra == "sparse_kl" else batched_extra
+    print(json.dumps(fn(args.steps, flush, torch.cuda.current_stream(), peak, peak_src)), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.extra:
+        return run_extra(args)
     return run_ours(args)
 
 

@@ -84,6 +84,17 @@ struct nmf_ctx {
   unsigned* d_counter = nullptr;  // completion counter of the fused epilogues
   bool lossFused = false;
   void* Vpad = nullptr;           // row-padded copy of V (tensor-core contexts, unaligned rows)
+  // batched NMF_BF16: the fused sweep's work items, tables and tensor maps
+  struct FuBatchState {
+    bool ok = false;
+    int c = 1, nitems = 0, layK = 32, totHc = 0;
+    int4* d_items = nullptr;       // launch order (longest first)
+    int* d_lossBase = nullptr;     // per launched item: its first objective partial
+    int* d_prefLoss = nullptr;     // per problem: first objective partial (count + 1 entries)
+    int* d_prefHc = nullptr;       // per problem: first 32-column block of the copies kernel
+    CUtensorMap* d_maps = nullptr; // 3 per problem
+    std::vector<int64_t> padOff;   // per problem: offset of its V in the padded copy (empty: no copy)
+  } fb;
   const void* vpadSrc = nullptr;
   bool vDirty = true;
   // CUDA graphs of step calls (see capture_step)
@@ -134,7 +145,21 @@ void free_all(nmf_ctx* c) {
   c->d_gW = c->d_gH = nullptr;
   c->d_kkt = nullptr;
   c->stageV = c->stageW = c->stageH = nullptr;
+  // every device pointer of the context went with the allocations: calls
+  // before the next prepare() (nmf_set_factors clears the status word when
+  // there is one) must not reach freed memory
+  c->d_status = nullptr;
+  c->d_lossPart = c->d_lossOut = nullptr;
+  c->tildeW = c->tildeH = nullptr;
+  c->d_normPart = nullptr;
+  c->d_counter = nullptr;
   c->sp = SparseKL();
+  // the padded copy of V went with the other allocations: the next upload
+  // allocates and fills it again
+  c->Vpad = nullptr;
+  c->vpadSrc = nullptr;
+  c->vDirty = true;
+  c->fb = nmf_ctx::FuBatchState();
 }
 
 nmf_status dalloc(nmf_ctx* c, void** p, size_t bytes) {
@@ -150,6 +175,9 @@ nmf_status dalloc(nmf_ctx* c, void** p, size_t bytes) {
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// Batched fused sweep: 128-column batches per work item for a chunk cap (the
+// autotuned parameter of batched contexts, 8 ... 128): 2 ... 32.
+int fu_batches(int cap) { return std::max(1, cap / 4); }
 
 struct Tiling {
   int rowTilesF, S, colTilesN, R;
@@ -298,6 +326,9 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
         probs[i].kp = (K + 15) & ~15;
         probs[i].fuS = std::max(1, tc_fused_clusters(probs[i], c->sms));
       }
+      // batched: items of fu_batches(chunkCap) 128-column batches, one slice each
+      if (c->batched && c->prec == NMF_BF16)
+        probs[i].fuS = (int)cdiv(cdiv(N, 128), (int64_t)fu_batches(c->chunkCap));
     }
     const int Smax = std::max({tl[i].S, probs[i].tcS, probs[i].fuS}), Rmax = std::max(tl[i].R, probs[i].tcR);
     const size_t FK = (size_t)F * K, KN = (size_t)K * N;
@@ -362,6 +393,79 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
     P.sWS = ptrs[0]; P.sWT = ptrs[1]; P.sHT = ptrs[2]; P.sHS = ptrs[3];
     P.sCW1 = ptrs[4]; P.sCW2 = ptrs[5]; P.sCH1 = ptrs[6]; P.sCH2 = ptrs[7];
   }
+  // batched NMF_BF16: per-problem TF32 shadows (sWS, sHT) and the fused
+  // sweep's work items (problem order for slices and objective partials,
+  // launched longest first)
+  if constexpr (std::is_same<T, float>::value) {
+    c->fb = nmf_ctx::FuBatchState();
+    if (c->batched && c->prec == NMF_BF16) {
+      int maxF = 0;
+      bool fits = true;
+      for (int i = 0; i < cnt; ++i) {
+        maxF = (int)std::max<int64_t>(maxF, c->F[i]);
+        fits = fits && c->K[i] <= 32;
+      }
+      fits = fits && maxF <= 1024 && tc_fused_batch_nv(32) >= 2;
+      if (fits) {
+        size_t total = 0;
+        std::vector<size_t> so(cnt);
+        for (int i = 0; i < cnt; ++i) {
+          Prob<T>& P = probs[i];
+          P.kp = (P.K + 15) & ~15;
+          P.ks = 32;
+          P.Fp = (P.F + 3) & ~int64_t(3);
+          P.Np = (P.N + 3) & ~int64_t(3);
+          so[i] = total;
+          total += align256(sizeof(T) * (size_t)P.F * P.ks) + align256(sizeof(T) * (size_t)P.N * P.ks);
+        }
+        void* sh = nullptr;
+        NMF_TRY(dalloc(c, &sh, total));
+        NMF_CU(cudaMemset(sh, 0, total));
+        for (int i = 0; i < cnt; ++i) {
+          Prob<T>& P = probs[i];
+          char* b = static_cast<char*>(sh) + so[i];
+          P.sWS = reinterpret_cast<T*>(b);
+          P.sHT = reinterpret_cast<T*>(b + align256(sizeof(T) * (size_t)P.F * P.ks));
+        }
+        const int cc = (int)cdiv(maxF, 128), B = fu_batches(c->chunkCap);
+        std::vector<int4> items;
+        std::vector<int> lossBase, prefLoss(cnt + 1), prefHc(cnt + 1);
+        prefLoss[0] = prefHc[0] = 0;
+        for (int i = 0; i < cnt; ++i) {
+          const int nb = (int)cdiv(c->N[i], 128), n = probs[i].fuS;
+          for (int q = 0; q < n; ++q) {
+            items.push_back(make_int4(i, (int)((int64_t)nb * q / n), (int)((int64_t)nb * (q + 1) / n), q));
+            lossBase.push_back(cc * (int)(items.size() - 1));
+          }
+          prefLoss[i + 1] = cc * (int)items.size();
+          prefHc[i + 1] = prefHc[i] + (int)cdiv(c->N[i], 32);
+        }
+        std::vector<int> order(items.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+          return items[a].z - items[a].y > items[b].z - items[b].y;
+        });
+        std::vector<int4> itemsL(items.size());
+        std::vector<int> baseL(items.size());
+        for (size_t q = 0; q < order.size(); ++q) { itemsL[q] = items[order[q]]; baseL[q] = lossBase[order[q]]; }
+        auto& fb = c->fb;
+        fb.c = cc;
+        fb.nitems = (int)items.size();
+        fb.layK = 32;
+        fb.totHc = prefHc[cnt];
+        NMF_TRY(dalloc(c, reinterpret_cast<void**>(&fb.d_items), sizeof(int4) * itemsL.size()));
+        NMF_TRY(dalloc(c, reinterpret_cast<void**>(&fb.d_lossBase), sizeof(int) * baseL.size()));
+        NMF_TRY(dalloc(c, reinterpret_cast<void**>(&fb.d_prefLoss), sizeof(int) * prefLoss.size()));
+        NMF_TRY(dalloc(c, reinterpret_cast<void**>(&fb.d_prefHc), sizeof(int) * prefHc.size()));
+        NMF_TRY(dalloc(c, reinterpret_cast<void**>(&fb.d_maps), sizeof(CUtensorMap) * 3 * (size_t)cnt));
+        NMF_CU(cudaMemcpy(fb.d_items, itemsL.data(), sizeof(int4) * itemsL.size(), cudaMemcpyHostToDevice));
+        NMF_CU(cudaMemcpy(fb.d_lossBase, baseL.data(), sizeof(int) * baseL.size(), cudaMemcpyHostToDevice));
+        NMF_CU(cudaMemcpy(fb.d_prefLoss, prefLoss.data(), sizeof(int) * prefLoss.size(), cudaMemcpyHostToDevice));
+        NMF_CU(cudaMemcpy(fb.d_prefHc, prefHc.data(), sizeof(int) * prefHc.size(), cudaMemcpyHostToDevice));
+        fb.ok = true;          // until the tensor maps fail to build (upload_table)
+      }
+    }
+  }
   void* d = nullptr;
   NMF_TRY(dalloc(c, &d, sizeof(Prob<T>) * cnt));
   pl.d_probs = static_cast<Prob<T>*>(d);
@@ -389,6 +493,7 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
   pl.d_prefH = tabs + 3 * (cnt + 1); pl.totH = ph[cnt];
   pl.d_prefK = tabs + 4 * (cnt + 1); pl.totK = pk[cnt];
   size_t lossLen = (size_t)std::max(pl.totRow, pl.totCol);
+  if constexpr (std::is_same<T, float>::value) lossLen = std::max<size_t>(lossLen, (size_t)c->fb.c * c->fb.nitems);
   if (!c->batched) lossLen = std::max<size_t>(lossLen, (size_t)std::max({tcRowGrid, tcColGrid, c->sms + 8}));
   NMF_TRY(dalloc(c, reinterpret_cast<void**>(&c->d_lossPart), sizeof(double) * lossLen));
   if (!c->batched) {
@@ -403,6 +508,35 @@ nmf_status build_plan(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
 
 template <typename T>
 nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
+  if constexpr (std::is_same<T, float>::value) {
+    auto& fb = c->fb;
+    if (c->batched && fb.ok) {
+      // row-padded packed copy of V when some problem's rows or base are not 16-byte aligned
+      bool aligned = (reinterpret_cast<uintptr_t>(c->Vp) & 15u) == 0;
+      for (int i = 0; i < c->count; ++i) aligned = aligned && (c->N[i] % 4 == 0) && ((c->F[i] * c->N[i]) % 4 == 0);
+      fb.padOff.clear();
+      if (!aligned) {
+        int64_t tot = 0;
+        for (int i = 0; i < c->count; ++i) {
+          fb.padOff.push_back(tot);
+          tot += c->F[i] * ((c->N[i] + 3) & ~int64_t(3));
+        }
+        if (!c->Vpad) NMF_TRY(dalloc(c, &c->Vpad, sizeof(float) * (size_t)tot));
+        if (c->vDirty || c->vpadSrc != c->Vp) {
+          int64_t oSrc = 0;
+          for (int i = 0; i < c->count; ++i) {
+            const int64_t Np = (c->N[i] + 3) & ~int64_t(3);
+            NMF_CU(cudaMemcpy2DAsync(static_cast<float*>(c->Vpad) + fb.padOff[i], sizeof(float) * Np,
+                                     static_cast<const float*>(c->Vp) + oSrc, sizeof(float) * c->N[i],
+                                     sizeof(float) * c->N[i], c->F[i], cudaMemcpyDeviceToDevice, c->stream));
+            oSrc += c->F[i] * c->N[i];
+          }
+          c->vpadSrc = c->Vp;
+          c->vDirty = false;
+        }
+      }
+    }
+  }
   size_t oW = 0, oH = 0, oV = 0;
   for (int i = 0; i < c->count; ++i) {
     Prob<T>& P = probs[i];
@@ -411,6 +545,15 @@ nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
       P.W = static_cast<T*>(c->Wp) + oW;
       P.H = static_cast<T*>(c->Hp) + oH;
       P.ldv = P.N;
+      if constexpr (std::is_same<T, float>::value) {
+        // the fused sweep streams V by TMA: rows and bases 16-byte aligned,
+        // else a row-padded packed copy (taken when V is set)
+        auto& fb = c->fb;
+        if (fb.ok && !fb.padOff.empty()) {
+          P.V = static_cast<const T*>(c->Vpad) + fb.padOff[i];
+          P.ldv = (P.N + 3) & ~int64_t(3);
+        }
+      }
     } else {
       P.V = static_cast<const T*>(c->V);
       P.W = static_cast<T*>(c->W);
@@ -434,6 +577,18 @@ nmf_status upload_table(nmf_ctx* c, Plan<T>& pl, std::vector<Prob<T>>& probs) {
       }
     }
     oW += (size_t)P.F * P.K; oH += (size_t)P.K * P.N; oV += (size_t)P.F * P.N;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    auto& fb = c->fb;
+    if (c->batched && fb.ok) {
+      std::vector<CUtensorMap> maps(3 * (size_t)c->count);
+      for (int i = 0; i < c->count && fb.ok; ++i) fb.ok = tc_fused_maps(probs[i], &maps[3 * (size_t)i]);
+      if (fb.ok)
+        NMF_CU(cudaMemcpyAsync(fb.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                               c->stream));
+      // a host-memory source: the copy must finish before `maps` goes away
+      NMF_CU(cudaStreamSynchronize(c->stream));
+    }
   }
   // 16-byte H epilogue: one float problem, N % 4 == 0 and the caller's H aligned
   pl.colVec4 = (!c->batched && c->count == 1 && sizeof(T) == 4 && c->N[0] % 4 == 0 &&
@@ -545,7 +700,8 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   const char* fcEnv = std::getenv("NMF_TC_FUSE_COPIES");
   const bool fuseCopies = !(fcEnv && fcEnv[0] == '0') && tci == 2 && joint && L == 1 && fuse && norm && wfirst &&
                           c->hpf[0].sWS;
-  bool haveCopies = fuseCopies && c->copiesValid;
+  const bool copiesIn = c->copiesValid;    // the copies of the current W, H exist (see the BF16 path too)
+  bool haveCopies = fuseCopies && copiesIn;
   c->copiesValid = false;
   auto row_sweep = [&](int wsel, int hsel, int dsel, int flags, const SideJob* side = nullptr) -> nmf_status {
     if constexpr (std::is_same<T, float>::value) {
@@ -648,11 +804,42 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   // from the previous call's last kernel while nothing changed W and H in
   // between (copiesValid), else from the copies kernel.
   if constexpr (std::is_same<T, float>::value) {
+    if (c->prec == NMF_BF16 && c->batched) {
+      // many problems: every iteration's copies of all W~, H~ | the fused
+      // sweep over every problem's work items (one launch) | the W updates
+      // from each problem's slices | normalisation; the objectives per problem
+      // from the fused sweep's partials
+      auto& fb = c->fb;
+      FuBatch b;
+      b.c = fb.c;
+      b.nitems = fb.nitems;
+      b.layK = fb.layK;
+      b.items = fb.d_items;
+      b.probs = pl.d_probs;
+      b.maps = fb.d_maps;
+      b.lossBase = fb.d_lossBase;
+      b.lossPart = lp;
+      for (int it = 0; it < iters; ++it) {
+        NMF_CU(timed(&c->timer, st, "begin_iteration", 1,
+                     [&] { return launch_fused_batch_copies(pl, fb.d_prefHc, fb.totHc, status, st); }));
+        NMF_CU(timed(&c->timer, st, "tc_fused", 1,
+                     [&] { return launch_tc_fused_batch(b, bp, status, c->waitLimitNs, c->extraArrivals, st); }));
+        NMF_CU(timed(&c->timer, st, "rows_epilogue", 1, [&] {
+          return launch_rows_epilogue<T>(pl, EPI_UPDATE, SEL_TILDE, 0, bp, nullptr, status, st, 3, EpiFuse());
+        }));
+        if (norm) NMF_CU(timed(&c->timer, st, "normalize", 2, [&] { return launch_normalize<T>(pl, status, st); }));
+      }
+      if (wantLoss)
+        NMF_CU(timed(&c->timer, st, "loss_finalize", 1,
+                     [&] { return launch_loss_finalize(fb.d_prefLoss, c->count, lp, c->d_lossOut, st); }));
+      c->lossFused = true;
+      c->copiesValid = false;
+      return NMF_OK;
+    }
     if (c->prec == NMF_BF16) {
       const Prob<float>& P0 = c->hpf[0];
       const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
-      const bool haveCopies = c->copiesValid;
-      c->copiesValid = false;
+      const bool haveCopies = copiesIn;
       for (int it = 0; it < iters; ++it) {
         const bool lossHere = wantLoss && it == iters - 1;
         if (it == 0 && !haveCopies)
@@ -976,10 +1163,12 @@ nmf_status step(nmf_ctx* c, bool joint, int32_t iters, double* loss_out, double*
   NMF_TRY(prepare(c));
   if (c->sparse) NMF_TRY(ensure_sparse(c));
   const bool tc = c->prec == NMF_TF32 || c->prec == NMF_BF16;
-  if (!c->sparse && tc && (c->batched || tc_kp(c->K[0]) > TC_KPMAX)) return NMF_EUNSUPPORTED;
+  if (!c->sparse && tc && ((c->batched && c->prec != NMF_BF16) || (!c->batched && tc_kp(c->K[0]) > TC_KPMAX)))
+    return NMF_EUNSUPPORTED;
   // NMF_BF16 is the fused single-read joint iteration: H first, L = 1, K <= 32, F <= 1024
   if (!c->sparse && c->prec == NMF_BF16 &&
-      (!joint || c->L != 1 || c->order == NMF_W_FIRST || !c->tcmaps.ok || !tc_fused_supported(c->hpf[0])))
+      (!joint || c->L != 1 || c->order == NMF_W_FIRST ||
+       (c->batched ? !c->fb.ok : (!c->tcmaps.ok || !tc_fused_supported(c->hpf[0])))))
     return NMF_EUNSUPPORTED;
   const bool wantLoss = loss_out != nullptr || loss_dev != nullptr;
   const bool readback = loss_dev == nullptr;
@@ -1170,6 +1359,7 @@ nmf_status nmf_batch_set_packed(nmf_ctx* c, const void* V_packed, void* W_packed
   invalidate_graphs(c);
   c->Vp = V_packed; c->Wp = W_packed; c->Hp = H_packed;
   c->tableDirty = true;
+  c->vDirty = true;
   if (c->d_status) {
     if (cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) != cudaSuccess) return NMF_ECUDA;
   }

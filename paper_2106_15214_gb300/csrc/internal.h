@@ -331,6 +331,32 @@ bool tc_fused_supported(const Prob<float>& P);
 int tc_fused_clusters(const Prob<float>& P, int sms);
 cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
                             int* status, uint64_t limitNs, unsigned extra, cudaStream_t st);
+// The same sweep over many problems in one launch (batched contexts): work
+// item i = {problem, first 128-column batch, end batch, partial slice of that
+// problem} runs on cluster i of c = ceil(max F / 128) blocks; the problems'
+// descriptors (device Prob array), tensor maps (maps[3 p + 0..2]: V, W~ rows
+// sWS, H~^T rows sHT, built by tc_fused_maps) and the index of each item's
+// first objective partial (lossBase) live in device memory.
+struct FuBatch {
+  int c = 1, nitems = 0, layK = 32;
+  const int4* items = nullptr;
+  const Prob<float>* probs = nullptr;
+  const CUtensorMap* maps = nullptr;
+  const int* lossBase = nullptr;
+  double* lossPart = nullptr;
+};
+cudaError_t launch_tc_fused_batch(const FuBatch& fb, const BetaParams& bp, int* status, uint64_t limitNs,
+                                  unsigned extra, cudaStream_t st);
+// V tile depth of the batched sweep's layout (0: does not fit).
+int tc_fused_batch_nv(int layK);
+// The three tensor maps of one problem for the fused sweep (false if V's rows
+// or the shadows are not 16-byte aligned).
+bool tc_fused_maps(const Prob<float>& P, CUtensorMap out[3]);
+// W~, H~ and their TF32 shadows sWS, sHT of every problem of a batched
+// context (the copies the batched fused sweep reads); blocks: the W blocks of
+// pl (prefW) then cdiv(N, 32) per problem (prefHc, totHc of them).
+cudaError_t launch_fused_batch_copies(const Plan<float>& pl, const int* prefHc, int totHc, const int* status,
+                                      cudaStream_t st);
 
 // Sparse beta = 1 path (sparse_kl.cu).
 struct SparseKL {

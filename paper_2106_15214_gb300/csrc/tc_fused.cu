@@ -122,10 +122,19 @@ struct FuParams {
   int ncl;           // clusters
   int nbatch;        // 128-column batches of V
   int nv;
+  int layK, laykp;   // the rank the shared-memory layout is sized for (many problems: the largest)
   double* lossPart;  // one partial per block
   int* status;
   uint64_t limitNs;  // bound of every wait
   unsigned extra;    // arrivals the cluster barriers expect beyond the c blocks (0; 1 in the timeout test)
+  // many problems in one launch: cluster i runs work item items[i] = {problem,
+  // first batch, end batch, partial slice}, reads the problem's descriptor
+  // from probs and its V, W~-row and H~^T tensor maps from maps[3 p ..], and
+  // writes its blocks' objective partials from lossPart[lossBase[i]] on
+  const int4* items;
+  const Prob<float>* probs;
+  const CUtensorMap* maps;
+  const int* lossBase;
 };
 
 // Bounded local wait shared by every role (gives up when another role did).
@@ -194,11 +203,12 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned 
   fence_mbar_init();
 }
 
-// One launch per iteration; grid = ncl clusters x c blocks.
-template <int BK>
+// One launch per iteration; grid = ncl clusters x c blocks. BATCH: the
+// clusters run work items of many problems (FuParams::items).
+template <int BK, bool BATCH>
 __global__ void __launch_bounds__(FU_THREADS, 1)
-tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmW,
-                const __grid_constant__ CUtensorMap tmH, Prob<float> P, BetaParams bp, FuParams S) {
+tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant__ CUtensorMap tmW0,
+                const __grid_constant__ CUtensorMap tmH0, Prob<float> P0, BetaParams bp, FuParams S) {
   pdl_trigger();
   extern __shared__ unsigned char smem_raw[];
   __shared__ FuBars bars;
@@ -208,14 +218,28 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   __shared__ double red[32];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K = P.K, kp = (K + 15) & ~15;
   const int c = S.c;
   const int r = (int)cluster_rank();                 // row tile of this block
   const int cl = (int)(blockIdx.x / (unsigned)c);
-  const int b0 = (int)((int64_t)cl * S.nbatch / S.ncl), b1 = (int)((int64_t)(cl + 1) * S.nbatch / S.ncl);
+  int pi = 0, b0, b1, slice, lossIdx;
+  if constexpr (BATCH) {
+    const int4 it = S.items[cl];
+    pi = it.x; b0 = it.y; b1 = it.z; slice = it.w;
+    lossIdx = S.lossBase[cl] + r;
+  } else {
+    b0 = (int)((int64_t)cl * S.nbatch / S.ncl);
+    b1 = (int)((int64_t)(cl + 1) * S.nbatch / S.ncl);
+    slice = cl;
+    lossIdx = (int)blockIdx.x;
+  }
+  const Prob<float>& P = BATCH ? S.probs[pi] : P0;
+  const CUtensorMap* tmV = BATCH ? S.maps + 3 * pi : &tmV0;
+  const CUtensorMap* tmW = BATCH ? S.maps + 3 * pi + 1 : &tmW0;
+  const CUtensorMap* tmH = BATCH ? S.maps + 3 * pi + 2 : &tmH0;
+  const int K = P.K, kp = (K + 15) & ~15;
   const int nb = b1 - b0;
   const int nv = S.nv;
-  const FuLayout L = fu_layout(K, kp, nv);
+  const FuLayout L = fu_layout(S.layK, S.laykp, nv);
   const int64_t m0 = (int64_t)r * 128;
   const uint64_t lim = S.limitNs;
   const int ntiles = 4 * nb;
@@ -226,9 +250,9 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   if (warp == 2) tmem_alloc(&tslot, FT_COLS);
   if (tid == 0) {
     s_abort = 0;
-    prefetch_tmap(&tmV);
-    prefetch_tmap(&tmW);
-    prefetch_tmap(&tmH);
+    prefetch_tmap(tmV);
+    prefetch_tmap(tmW);
+    prefetch_tmap(tmH);
     fu_init_bars(bars, nv, c, S.extra);
   }
   fence_before_sync();
@@ -237,7 +261,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   if (warp == 1 && elect_one()) {
     for (int t = 0; t < vPre; ++t) {
       mbar_arrive_expect_tx(&bars.vfull[t], FU_TB);
-      tma_load_2d(base + L.v0 + t * FU_TB, &tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[t]);
+      tma_load_2d(base + L.v0 + t * FU_TB, tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[t]);
     }
   }
   __syncwarp();
@@ -274,7 +298,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
     // ---------------- operand loads ----------------
     if (nbr > 0 && elect_one()) {
       mbar_arrive_expect_tx(&bars.once, FU_TB);
-      tma_load_2d(base + L.wt, &tmW, 0, (int)m0, &bars.once);          // W~ rows (TF32 copy)
+      tma_load_2d(base + L.wt, tmW, 0, (int)m0, &bars.once);           // W~ rows (TF32 copy)
     }
     __syncwarp();
     int issued = 0;
@@ -285,7 +309,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
         break;
       if (elect_one()) {
         mbar_arrive_expect_tx(&bars.fafull[s], FU_TB);
-        tma_load_2d(base + L.fa0 + s * FU_TB, &tmH, 0, (int)(128 * (int64_t)(b0 + j)), &bars.fafull[s]);
+        tma_load_2d(base + L.fa0 + s * FU_TB, tmH, 0, (int)(128 * (int64_t)(b0 + j)), &bars.fafull[s]);
       }
       __syncwarp();
     }
@@ -308,7 +332,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
         break;
       if (elect_one()) {
         mbar_arrive_expect_tx(&bars.vfull[sv], FU_TB);
-        tma_load_2d(base + L.v0 + sv * FU_TB, &tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[sv]);
+        tma_load_2d(base + L.v0 + sv * FU_TB, tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[sv]);
       }
       __syncwarp();
     }
@@ -654,7 +678,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   __syncthreads();
   if (write) {
     const int nrows = (int)(P.F - m0 < 128 ? P.F - m0 : 128);
-    float* outP = P.rowPart + (int64_t)cl * 2 * P.F * K + m0 * K;
+    float* outP = P.rowPart + (int64_t)slice * 2 * P.F * K + m0 * K;
     float* outQ = outP + P.F * K;
     for (int rr = warp; rr < nrows; rr += FU_THREADS / 32)
       for (int cc = lane; cc < K; cc += 32) {
@@ -663,7 +687,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
       }
   }
   const double unitLoss = block_sum_ff(lossHi, lossLo, reinterpret_cast<float2*>(red));
-  if (tid == 0) S.lossPart[blockIdx.x] = unitLoss;
+  if (tid == 0) S.lossPart[lossIdx] = unitLoss;
   fence_before_sync();
   __syncthreads();
   if (s_abort) mbar_wait(&bars.done, 0u, 100000000ull);
@@ -672,9 +696,56 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__
   if (warp == 2) tmem_dealloc(tbase, FT_COLS);
 }
 
+// W~ = W, H~ = H and their TF32 shadows (sWS: F x ks rows, sHT: N x ks rows)
+// of every problem of a batched context: blocks [0, totW) take EW entries of
+// some W (prefW), the others 32 columns of some H (prefHc), transposed through
+// shared memory so that both the reads of H and the writes of sHT coalesce.
+__global__ void __launch_bounds__(EW)
+fused_batch_copies_kernel(const Prob<float>* __restrict__ probs, int count, const int* __restrict__ prefW, int totW,
+                          const int* __restrict__ prefHc, const int* __restrict__ status) {
+  if (*status) return;
+  __shared__ float tile[32][33];
+  int b = blockIdx.x;
+  if (b < totW) {
+    const int pi = find_problem(prefW, count, b);
+    const Prob<float>& P = probs[pi];
+    const int64_t idx = (int64_t)(b - prefW[pi]) * EW + threadIdx.x;
+    if (idx < P.F * P.K) {
+      const float w = P.W[idx];
+      P.Wt[idx] = w;
+      const int64_t f = idx / P.K, k = idx - f * P.K;
+      P.sWS[f * P.ks + k] = tf32_round(w);
+    }
+    return;
+  }
+  b -= totW;
+  const int pi = find_problem(prefHc, count, b);
+  const Prob<float>& P = probs[pi];
+  const int64_t n0 = (int64_t)(b - prefHc[pi]) * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = w; k < P.K; k += EW / 32)
+    if (n0 + lane < P.N) {
+      const float h = P.H[(int64_t)k * P.N + n0 + lane];
+      P.Ht[(int64_t)k * P.N + n0 + lane] = h;
+      tile[lane][k] = tf32_round(h);
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * P.K; i += EW) {
+    const int nl = i / P.K, k = i - nl * P.K;
+    if (n0 + nl < P.N) P.sHT[(n0 + nl) * P.ks + k] = tile[nl][k];
+  }
+}
+
 }  // namespace
 
 // ---- host ------------------------------------------------------------------
+
+cudaError_t launch_fused_batch_copies(const Plan<float>& pl, const int* prefHc, int totHc, const int* status,
+                                      cudaStream_t st) {
+  fused_batch_copies_kernel<<<(unsigned)(pl.totW + totHc), EW, 0, st>>>(pl.d_probs, pl.count, pl.d_prefW, pl.totW,
+                                                                         prefHc, status);
+  return cudaGetLastError();
+}
 
 bool tc_fused_supported(const Prob<float>& P) {
   return P.sWS && P.kp <= 32 && P.F <= 1024 && fu_pick_nv(P.K, P.kp) >= 2;
@@ -685,7 +756,7 @@ int tc_fused_clusters(const Prob<float>& P, int sms) {
   const int nbatch = (int)((P.N + 127) / 128);
   const int nv = fu_pick_nv(P.K, P.kp);
   const size_t sm = 1024 + fu_layout(P.K, P.kp, nv).total;
-  auto kern = tc_fused_kernel<BK_GENERAL>;
+  auto kern = tc_fused_kernel<BK_GENERAL, false>;
   if (ensure_smem_attr(reinterpret_cast<const void*>(kern), sm) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -721,6 +792,8 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   S.nbatch = (int)((P.N + 127) / 128);
   S.ncl = ncl;
   S.nv = fu_pick_nv(P.K, P.kp);
+  S.layK = P.K;
+  S.laykp = P.kp;
   S.lossPart = lossPart;
   S.status = status;
   S.limitNs = limitNs;
@@ -753,8 +826,65 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   cudaError_t e = cudaSuccess;
 #define NMF_FU_CASE(BKV)                                                                   \
   case BKV:                                                                                \
-    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV>), sm);         \
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV>, tmV, m.wsA, m.htB, P, bp, S); \
+    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, false>), sm);  \
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, false>, tmV, m.wsA, m.htB, P, bp, S); \
+    break;
+  switch (bp.kind) {
+    NMF_FU_CASE(BK_IS)
+    NMF_FU_CASE(BK_KL)
+    NMF_FU_CASE(BK_EUC)
+    NMF_FU_CASE(BK_B15)
+    NMF_FU_CASE(BK_GENERAL)
+  }
+#undef NMF_FU_CASE
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+int tc_fused_batch_nv(int layK) { return fu_pick_nv(layK, (layK + 15) & ~15); }
+
+cudaError_t launch_tc_fused_batch(const FuBatch& fb, const BetaParams& bp, int* status, uint64_t limitNs,
+                                  unsigned extra, cudaStream_t st) {
+  FuParams S;
+  memset(&S, 0, sizeof(S));
+  S.c = fb.c;
+  S.ncl = fb.nitems;
+  S.nbatch = 0;
+  S.layK = fb.layK;
+  S.laykp = (fb.layK + 15) & ~15;
+  S.nv = fu_pick_nv(S.layK, S.laykp);
+  S.lossPart = fb.lossPart;
+  S.status = status;
+  S.limitNs = limitNs;
+  S.extra = extra;
+  S.items = fb.items;
+  S.probs = fb.probs;
+  S.maps = fb.maps;
+  S.lossBase = fb.lossBase;
+  if (S.nv < 2 || fb.nitems < 1 || S.c < 1 || S.c > 8 || S.laykp > 32) return cudaErrorInvalidValue;
+  const size_t sm = 1024 + fu_layout(S.layK, S.laykp, S.nv).total;
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  Prob<float> P0;
+  memset(static_cast<void*>(&P0), 0, sizeof(P0));
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(S.c * fb.nitems));
+  cfg.blockDim = dim3(FU_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S.c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaSuccess;
+#define NMF_FU_CASE(BKV)                                                                  \
+  case BKV:                                                                               \
+    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, true>), sm);  \
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, true>, none, none, none, P0, bp, S); \
     break;
   switch (bp.kind) {
     NMF_FU_CASE(BK_IS)

@@ -156,6 +156,13 @@ bool tc_build_maps(const Prob<float>& P, TcMaps* m) {
   return ok;
 }
 
+bool tc_fused_maps(const Prob<float>& P, CUtensorMap out[3]) {
+  if (!P.sWS || !P.sHT || P.kp > 32) return false;
+  const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
+  return tc_map_v(P, true, &out[0]) && map2d(&out[1], P.sWS, P.ks, P.F, P.ks, 32, MT, SW) &&
+         map2d(&out[2], P.sHT, P.ks, P.N, P.ks, 32, BT * TL, SW);
+}
+
 int tc_ws_capacity(int kp, int csize) {
   if (kp > 64 || kp < 16) return 0;
   int nop = 0, nv = 0;
