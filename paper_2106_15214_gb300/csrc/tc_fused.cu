@@ -127,6 +127,8 @@ struct FuParams {
   int* status;
   uint64_t limitNs;  // bound of every wait
   unsigned extra;    // arrivals the cluster barriers expect beyond the c blocks (0; 1 in the timeout test)
+  int early;         // launched without programmatic dependent launch: the operand copies are complete at
+                     // entry, so their first loads go out with the first V tiles
   // many problems in one launch: cluster i runs work item items[i] = {problem,
   // first batch, end batch, partial slice}, reads the problem's descriptor
   // from probs and its V, W~-row and H~^T tensor maps from maps[3 p ..], and
@@ -264,6 +266,15 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       tma_load_2d(base + L.v0 + t * FU_TB, tmV, (int)(128 * (int64_t)b0 + 32 * t), (int)m0, &bars.vfull[t]);
     }
   }
+  const int faPre = (S.early && nb > 0) ? (nb < 2 ? nb : 2) : 0;   // H~^T batches loaded before the wait
+  if (warp == 0 && faPre > 0 && elect_one()) {
+    mbar_arrive_expect_tx(&bars.once, FU_TB);
+    tma_load_2d(base + L.wt, tmW, 0, (int)m0, &bars.once);           // W~ rows (TF32 copy)
+    for (int j = 0; j < faPre; ++j) {
+      mbar_arrive_expect_tx(&bars.fafull[j], FU_TB);
+      tma_load_2d(base + L.fa0 + j * FU_TB, tmH, 0, (int)(128 * (int64_t)(b0 + j)), &bars.fafull[j]);
+    }
+  }
   __syncwarp();
   pdl_wait();
   // W~^T (bf16, the B operand of the H contraction) from the full-precision
@@ -296,13 +307,17 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
 
   if (warp == 0) {
     // ---------------- operand loads ----------------
-    if (nbr > 0 && elect_one()) {
+    if (faPre == 0 && nbr > 0 && elect_one()) {
       mbar_arrive_expect_tx(&bars.once, FU_TB);
       tma_load_2d(base + L.wt, tmW, 0, (int)m0, &bars.once);           // W~ rows (TF32 copy)
     }
     __syncwarp();
-    int issued = 0;
-    for (int j = 0; j < nbr; ++j, ++issued) {
+    if (nbr == 0 && faPre > 0) {                       // issued before the skip decision: wait for them
+      mbar_wait(&bars.once, 0u, 100000000ull);
+      for (int j = 0; j < faPre; ++j) mbar_wait(&bars.fafull[j], 0u, 100000000ull);
+    }
+    int issued = faPre < nbr ? faPre : nbr;
+    for (int j = issued; j < nbr; ++j, ++issued) {
       const int s = j & 1;
       if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.fafree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
                                                        S.status, lim)))
@@ -823,6 +838,7 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   // it on (A/B measurement).
   static const bool pdl = std::getenv("NMF_FU_PDL") && std::atoi(std::getenv("NMF_FU_PDL")) == 1;
   cfg.numAttrs = pdl ? 2 : 1;
+  S.early = pdl ? 0 : 1;
   cudaError_t e = cudaSuccess;
 #define NMF_FU_CASE(BKV)                                                                   \
   case BKV:                                                                                \
@@ -861,6 +877,7 @@ cudaError_t launch_tc_fused_batch(const FuBatch& fb, const BetaParams& bp, int* 
   S.probs = fb.probs;
   S.maps = fb.maps;
   S.lossBase = fb.lossBase;
+  S.early = 1;                                        // launched without programmatic dependent launch
   if (S.nv < 2 || fb.nitems < 1 || S.c < 1 || S.c > 8 || S.laykp > 32) return cudaErrorInvalidValue;
   const size_t sm = 1024 + fu_layout(S.layK, S.laykp, S.nv).total;
   CUtensorMap none;

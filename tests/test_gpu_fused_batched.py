@@ -167,3 +167,34 @@ def test_padded_v_is_rebuilt_with_the_plan(lib):
         assert rel(W.double().cpu().numpy(), Wo) < TOL_WH
         assert rel(H.double().cpu().numpy(), Ho) < TOL_WH
         m.close()
+
+
+def test_batched_cluster_wait_timeout_returns_etimeout(lib):
+    """The many-problem launch shares the single-problem kernel's bounded
+    cluster waits: with one arrival too many expected and a 2 ms limit every
+    such wait gives up, the step returns NMF_ETIMEOUT with W and H restored,
+    and with the defaults back the same context computes the oracle's iterate."""
+    import torch
+    from paper_2106_15214_gb300.binding import BatchedNMF, NMF_ETIMEOUT, NMFError, check
+    probs = inputs.batched_hyperspectral(count=6, F_range=(100, 250), N_range=(300, 900), K_range=(4, 24), seed=7)
+    shapes = [p.shape for p in probs]
+    Vp, Wp, Hp = pack(probs)
+    b = BatchedNMF(shapes, 1.5, precision="bf16", order="H")
+    Vd, Wd, Hd = dev(Vp), dev(Wp), dev(Hp)
+    W1, H1 = Wd.clone(), Hd.clone()
+    b.set_packed(Vd, Wd, Hd)
+    check(lib.nmf_set_barrier_test(b._ctx, 2_000_000, 1), "nmf_set_barrier_test")
+    with pytest.raises(NMFError) as e:
+        b.step_joint(1)
+    assert e.value.code == NMF_ETIMEOUT
+    torch.cuda.synchronize()
+    assert torch.equal(Wd, W1) and torch.equal(Hd, H1)
+    check(lib.nmf_set_barrier_test(b._ctx, 1_000_000_000, 0), "nmf_set_barrier_test")
+    b.set_packed(Vd, Wd, Hd)
+    b.step_joint(1)
+    Ws = unpack(Wd.double().cpu().numpy(), shapes, "W")
+    Hs = unpack(Hd.double().cpu().numpy(), shapes, "H")
+    b.close()
+    for i, p in enumerate(probs):
+        Wo, Ho, _ = O.run(p.V, p.W0, p.H0, 1.5, iters=1, order="H", eps=1e-30)
+        assert rel(Ws[i], Wo) < TOL_WH and rel(Hs[i], Ho) < TOL_WH, i
