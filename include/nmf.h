@@ -63,8 +63,13 @@ typedef enum {
   NMF_FP32 = 1,  /* float storage and arithmetic (SIMT FFMA) */
   NMF_TF32 = 2,  /* float storage; products on tensor cores (tcgen05 kind::tf32),
                     FP32 accumulation, powers in FP32, loss accumulated in FP64 */
-  NMF_BF16 = 3   /* float storage; tensor-core operands rounded to bf16
-                    (tcgen05 kind::f16), FP32 accumulation */
+  NMF_BF16 = 3   /* float storage; the fused single-read JMM iteration: the
+                    product Vt on tensor cores in TF32 (kind::tf32), A, B,
+                    W~ and chi rounded to bf16 for both contractions
+                    (kind::f16), FP32 accumulation, powers in FP32, loss in
+                    FP64. Dense single problems and batched contexts,
+                    nmf_step_joint only, L = 1, NMF_H_FIRST, K <= 32,
+                    F <= 1024; anything else returns NMF_EUNSUPPORTED. */
 } nmf_precision;
 
 typedef enum {
@@ -113,7 +118,9 @@ nmf_status nmf_set_floor(nmf_ctx* ctx, double eps);
  * contexts, whose work items are (problem, chunk of 32-wide tiles)): times
  * `trials` >= 1 joint steps for each cap in {8, 16, 32, 64, 128} on the number
  * of tiles one block sums (more chunks: more, shorter blocks and more partial
- * slices) and keeps the fastest. W, H and the status word are restored after
+ * slices) and keeps the fastest; for a batched NMF_BF16 context the cap sets
+ * the length of the fused sweep's work items instead (cap / 4 batches of 128
+ * columns per item). W, H and the status word are restored after
  * every trial, so the call leaves the factors as it found them. Choices are
  * cached per process under a shape signature (count, sums of F and N, largest
  * K, beta, precision, SM count); a cached signature returns at once. The cap
@@ -143,8 +150,8 @@ nmf_status nmf_set_csr(nmf_ctx* ctx, int64_t nnz, const int32_t* rowptr,
 
 /* Borrows the factors (device): W F x K, H K x N, updated in place. A step
  * may leave in the context the operand copies of the W and H it returns
- * (NMF_TF32, W first), which the next step then uses instead of copying them
- * again: after writing W or H in place between steps, call nmf_set_factors
+ * (NMF_TF32 W first, and NMF_BF16), which the next step then uses instead of
+ * copying them again: after writing W or H in place between steps, call nmf_set_factors
  * again (same pointers are fine), which drops those copies and clears the
  * status word. */
 nmf_status nmf_set_factors(nmf_ctx* ctx, void* W_dev, void* H_dev);
