@@ -12,7 +12,7 @@ kernel's and the whole step's HBM roofline, the host-buffer end-to-end rate,
 the CPU oracle's rate, the time to fixed objective targets D* and to the
 paper's stopping rule of JMM against alternating MU (BMM) on the same GPU,
 and extra workloads (the same problem at N = 200000, the TF32 two-sweep
-form, sparse KL count data, 512 batched problems).
+form, the adjoint, sparse KL count data, 512 batched problems).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -565,6 +565,36 @@ def dense_extra(p, beta, precision, order, steps, flush, stream, peak, peak_src,
     return out
 
 
+def grad_extra(p, beta, steps, flush, stream, peak, peak_src):
+    """The adjoint (a10): nmf_grad on the workload in FP32 (both gradients at
+    the current factors from one pass over V, the product recomputed per
+    tile; the objective beside it): time per call and the HBM fraction
+    against V once + W, H read + both gradients written; the FP64 oracle's
+    gradient on a column sample of the same data beside it."""
+    import torch
+    import oracle as O
+    from paper_2106_15214_gb300.binding import NMF
+    F, N, K = p.shape
+    m, V, W, H = dense_context(p, beta, "fp32", "W")
+    gW, gH = torch.empty_like(W), torch.empty_like(H)
+    for _ in range(3):
+        m.grad(gW, gH, want_loss=True)
+    torch.cuda.synchronize()
+    ms = timed_steps(lambda i: m.grad(gW, gH, want_loss=True), steps, flush, stream)
+    per = sum(ms) / len(ms)
+    ab = 4 * (F * N + 2 * (F * K + K * N))
+    m.close()
+    Ns = min(N, 2000)
+    t0 = time.perf_counter()
+    O.gradients(p.V[:, :Ns], p.W0, p.H0[:, :Ns], beta)
+    t_or = (time.perf_counter() - t0) * N / Ns
+    return {"workload": "nmf_grad, FP32, " + f"F={F} N={N} K={K} beta={beta}", "ms_per_call": per,
+            "calls_per_s": 1e3 / per, "algorithmic_bytes": ab, "achieved_GBs": ab / (per / 1e3) / 1e9,
+            "frac": ab / (per / 1e3) / 1e9 / peak, "peak_source": peak_src,
+            "oracle_s_per_call": t_or, "oracle_sample": f"first {Ns} of {N} columns, scaled to the full N",
+            "note": "each call synchronises (the objective is read back), as a training step would"}
+
+
 def sparse_extra(steps, flush, stream, peak, peak_src, tol_iters=2000):
     """Sparse KL (Sec. 4.4 stand-in, 20000 x 100000, 0.1 %, K = 50, CSR FP32):
     nnz/s of JMM and BMM and the HBM fraction against an iteration's
@@ -795,6 +825,7 @@ def run_ours(args):
             if args.workload == "spectrogram":
                 extras["tf32_two_sweeps"] = dense_extra(p, beta, "tf32", "W", 200, flush, stream, peak, peak_src,
                                                         "spectrogram")
+                extras["adjoint"] = grad_extra(p, beta, 50, flush, stream, peak, peak_src)
                 big, _ = problem("spectrogram_large")
                 extras["spectrogram_large"] = dense_extra(big, beta, precision, order, 100, flush, stream, peak,
                                                           peak_src, "spectrogram_large")

@@ -191,3 +191,45 @@ def test_cluster_wait_timeout_returns_etimeout(lib):
     Wo, Ho, _ = oracle_h_first(V, W0, H0, 1.0)
     assert rel(W.double().cpu().numpy(), Wo) < TOL_WH and rel(H.double().cpu().numpy(), Ho) < TOL_WH
     m.close()
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0])
+def test_kappa_and_no_normalisation(lib, beta):
+    """kappa > 0 (Sec. 4.1.3: added to V and to every product) and the step
+    without the normalisation (the last kernel then only makes the next
+    iteration's copies), three iterations in one call."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    V, W0, H0 = problem(300, 700, 20, seed=21)
+    for kappa, normalize in ((0.05, True), (0.0, False), (0.05, False)):
+        m = NMF(300, 700, 20, beta, precision="bf16", order="H", kappa=kappa, normalize=normalize)
+        W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+        H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+        m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
+        m.set_factors(W, H)
+        loss = m.step_joint(3)
+        Wo, Ho, lo = O.run(V, W0, H0, beta, iters=3, order="H", kappa=kappa, do_normalize=normalize, eps=1e-30)
+        assert rel(W.double().cpu().numpy(), Wo) < 2 * TOL_WH, (kappa, normalize)
+        assert rel(H.double().cpu().numpy(), Ho) < 2 * TOL_WH, (kappa, normalize)
+        assert loss == pytest.approx(lo[2], rel=TOL_D), (kappa, normalize)
+        m.close()
+
+
+def test_floor_matches_the_constrained_update(lib):
+    """nmf_set_floor(eps): every update clamped to eps (the constraint of eqs.
+    Wll / Hll), here with eps inside the range of the first update."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    V, W0, H0 = problem(200, 400, 12, seed=22)
+    W1, H1, _ = O.run(V, W0, H0, 0.0, iters=1, order="H", eps=0.0)
+    eps = float(np.quantile(np.concatenate([W1.ravel(), H1.ravel()]), 0.2))
+    m = NMF(200, 400, 12, 0.0, precision="bf16", order="H", floor=eps)
+    W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+    H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+    m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
+    m.set_factors(W, H)
+    m.step_joint(2)
+    Wo, Ho, _ = O.run(V, W0, H0, 0.0, iters=2, order="H", eps=eps)
+    Wg, Hg = W.double().cpu().numpy(), H.double().cpu().numpy()
+    assert rel(Wg, Wo) < 2 * TOL_WH and rel(Hg, Ho) < 2 * TOL_WH
+    m.close()
