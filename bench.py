@@ -566,33 +566,36 @@ def dense_extra(p, beta, precision, order, steps, flush, stream, peak, peak_src,
 
 
 def grad_extra(p, beta, steps, flush, stream, peak, peak_src):
-    """The adjoint (a10): nmf_grad on the workload in FP32 (both gradients at
-    the current factors from one pass over V, the product recomputed per
-    tile; the objective beside it): time per call and the HBM fraction
-    against V once + W, H read + both gradients written; the FP64 oracle's
-    gradient on a column sample of the same data beside it."""
+    """The adjoint (a10): nmf_grad on the workload (both gradients at the
+    current factors and the objective) on a BF16 context (the fused sweep's
+    adjoint mode: one read of V) and on an FP32 context (the SIMT sweeps: two
+    reads of V): time per call and the HBM fraction against V once + W, H
+    read + both gradients written; the FP64 oracle's gradient on a column
+    sample beside it."""
     import torch
     import oracle as O
-    from paper_2106_15214_gb300.binding import NMF
     F, N, K = p.shape
-    m, V, W, H = dense_context(p, beta, "fp32", "W")
-    gW, gH = torch.empty_like(W), torch.empty_like(H)
-    for _ in range(3):
-        m.grad(gW, gH, want_loss=True)
-    torch.cuda.synchronize()
-    ms = timed_steps(lambda i: m.grad(gW, gH, want_loss=True), steps, flush, stream)
-    per = sum(ms) / len(ms)
     ab = 4 * (F * N + 2 * (F * K + K * N))
-    m.close()
+    out = {"workload": f"nmf_grad, F={F} N={N} K={K} beta={beta}", "algorithmic_bytes": ab,
+           "note": "each call synchronises (the objective is read back), as a training step would"}
+    for prec, order in (("bf16", "H"), ("fp32", "W")):
+        m, V, W, H = dense_context(p, beta, prec, order)
+        gW, gH = torch.empty_like(W), torch.empty_like(H)
+        for _ in range(3):
+            m.grad(gW, gH, want_loss=True)
+        torch.cuda.synchronize()
+        ms = timed_steps(lambda i: m.grad(gW, gH, want_loss=True), steps, flush, stream)
+        per = sum(ms) / len(ms)
+        m.close()
+        out[prec] = {"ms_per_call": per, "calls_per_s": 1e3 / per, "achieved_GBs": ab / (per / 1e3) / 1e9,
+                     "frac": ab / (per / 1e3) / 1e9 / peak}
     Ns = min(N, 2000)
     t0 = time.perf_counter()
     O.gradients(p.V[:, :Ns], p.W0, p.H0[:, :Ns], beta)
-    t_or = (time.perf_counter() - t0) * N / Ns
-    return {"workload": "nmf_grad, FP32, " + f"F={F} N={N} K={K} beta={beta}", "ms_per_call": per,
-            "calls_per_s": 1e3 / per, "algorithmic_bytes": ab, "achieved_GBs": ab / (per / 1e3) / 1e9,
-            "frac": ab / (per / 1e3) / 1e9 / peak, "peak_source": peak_src,
-            "oracle_s_per_call": t_or, "oracle_sample": f"first {Ns} of {N} columns, scaled to the full N",
-            "note": "each call synchronises (the objective is read back), as a training step would"}
+    out["oracle_s_per_call"] = (time.perf_counter() - t0) * N / Ns
+    out["oracle_sample"] = f"first {Ns} of {N} columns, scaled to the full N"
+    out["peak_source"] = peak_src
+    return out
 
 
 def sparse_extra(steps, flush, stream, peak, peak_src, tol_iters=2000):

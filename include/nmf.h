@@ -192,7 +192,10 @@ nmf_status nmf_loss(nmf_ctx* ctx, double* out_host);
  * residuals (Sec. 4.1.5); equivalently the MU denominator minus numerator.
  * gW_dev, gH_dev are caller-owned device buffers of the context's element
  * type. If loss_out is not NULL it receives the loss at (W, H) and the call
- * synchronises. */
+ * synchronises. NMF_FP64 / NMF_FP32 / NMF_TF32 contexts run the SIMT sweeps
+ * (TF32: in FP32); a dense NMF_BF16 context runs the fused single-read sweep
+ * in its adjoint mode (one read of V, bf16 contractions: relative error of
+ * each of the two terms ~1e-2). */
 nmf_status nmf_grad(nmf_ctx* ctx, void* gW_dev, void* gH_dev, double* loss_out);
 
 /* KKT residuals res(W) = ||min{W, gW}||_1 / (FK), res(H) = ||min{H, gH}||_1 / (KN)

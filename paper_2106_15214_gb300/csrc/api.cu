@@ -1415,6 +1415,38 @@ nmf_status nmf_grad(nmf_ctx* c, void* gW_dev, void* gH_dev, double* loss_out) {
   if (!c || !gW_dev || !gH_dev) return NMF_EINVAL;
   if (c->batched) return NMF_EUNSUPPORTED;
   if (!data_ready(c)) return NMF_ENOTREADY;
+  // NMF_BF16 dense contexts: the fused single-read sweep in its adjoint mode
+  // (one read of V: both gradients and the objective, bf16 contractions)
+  if (c->prec == NMF_BF16 && !c->sparse) {
+    nmf_status s = prepare(c);
+    if (s == NMF_OK && c->tcmaps.ok && tc_fused_supported(c->hpf[0])) {
+      const Prob<float>& P0 = c->hpf[0];
+      const BetaParams bp = beta_params(c);
+      const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
+      const bool wantLoss = loss_out != nullptr;
+      int* status = c->d_status;
+      double* lp = c->d_lossPart;
+      cudaStream_t st = c->stream;
+      invalidate_graphs(c);
+      s = cu(launch_tc_copies<float>(P0, true, true, true, status, st));
+      if (s == NMF_OK)
+        s = cu(launch_tc_fused(P0, c->tcmaps, bp, ncl, lp, status, c->waitLimitNs, c->extraArrivals, st,
+                               static_cast<float*>(gH_dev)));
+      EpiFuse f;
+      f.flags = wantLoss ? FUSE_LOSS : 0;
+      f.lossPart = lp;
+      f.lossBlocks = cgrid;
+      f.lossOut = c->d_lossOut;
+      f.counter = c->d_counter;
+      if (s == NMF_OK)
+        s = cu(launch_rows_epilogue<float>(c->pf, EPI_GRAD, SEL_TILDE, 0, bp, static_cast<float*>(gW_dev), status, st,
+                                           3, f));
+      c->copiesValid = s == NMF_OK;      // the copies are of the current W, H
+      if (s == NMF_OK && wantLoss) s = sync_and_check(c, true, loss_out);
+      return s;
+    }
+    if (s != NMF_OK) return s;
+  }
   c->copiesValid = false;
   nmf_precision keep = c->prec;
   if (keep == NMF_TF32 || keep == NMF_BF16) c->prec = NMF_FP32;

@@ -329,8 +329,11 @@ bool tc_fused_supported(const Prob<float>& P);
 // Clusters of ceil(F / 128) blocks that can be resident at once (at most the
 // number of 128-column batches); 0 when the kernel cannot launch.
 int tc_fused_clusters(const Prob<float>& P, int sms);
+// gH not null: the adjoint instead of the update (H untouched): grad_H = W~^T (B - A)
+// into gH, and slices of P = A H~^T, Q = B H~^T (grad_W = Q - P by the W epilogue's
+// EPI_GRAD mode).
 cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
-                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st);
+                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st, float* gH = nullptr);
 // The same sweep over many problems in one launch (batched contexts): work
 // item i = {problem, first 128-column batch, end batch, partial slice of that
 // problem} runs on cluster i of c = ceil(max F / 128) blocks; the problems'

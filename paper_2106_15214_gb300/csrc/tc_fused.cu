@@ -129,6 +129,9 @@ struct FuParams {
   unsigned extra;    // arrivals the cluster barriers expect beyond the c blocks (0; 1 in the timeout test)
   int early;         // launched without programmatic dependent launch: the operand copies are complete at
                      // entry, so their first loads go out with the first V tiles
+  float* gH;         // not null: the adjoint instead of the update: the exchange writes
+                     // grad_H = W~^T (B - A) here and pushes chi_1 = chi_2 = H~, so the W
+                     // contraction gives P = A H~^T, Q = B H~^T (grad_W = Q - P); H is not written
   // many problems in one launch: cluster i runs work item items[i] = {problem,
   // first batch, end batch, partial slice}, reads the problem's descriptor
   // from probs and its V, W~-row and H~^T tensor maps from maps[3 p ..], and
@@ -614,7 +617,10 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
         for (int i = 0; i < 4; ++i) {
           const int64_t n = nb0 + n4 + i;
           c1[i] = c2[i] = 0.f;
-          if (n < P.N) {
+          if (n < P.N && S.gH) {                    // the adjoint (Sec. 4.1.5's gradient)
+            S.gH[(int64_t)k * P.N + n] = hd[i] - hn[i];
+            c1[i] = c2[i] = ht[i];
+          } else if (n < P.N) {
             const float h = apply_floor(ht[i] * mu_ratio<BK, float>(hn[i], hd[i], gam), flo);
             if (!isfinite(h)) atomicExch(S.status, 4);
             if (task == x) hkeep[i] = h;            // this thread's first task: stored after the handshake
@@ -641,7 +647,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       }
       {                                             // H of this thread's first task, now off the fence's path
         const int task = x, k = (tLo + task) >> 5, n4 = 4 * ((tLo + task) & 31);
-        if (go && task < ntask)
+        if (go && task < ntask && !S.gH)
           #pragma unroll
           for (int i = 0; i < 4; ++i)
             if (nb0 + n4 + i < P.N) P.H[(int64_t)k * P.N + nb0 + n4 + i] = hkeep[i];
@@ -800,9 +806,10 @@ int tc_fused_clusters(const Prob<float>& P, int sms) {
 }
 
 cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
-                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st) {
+                            int* status, uint64_t limitNs, unsigned extra, cudaStream_t st, float* gH) {
   FuParams S;
   memset(&S, 0, sizeof(S));
+  S.gH = gH;
   S.c = (int)((P.F + 127) / 128);
   S.nbatch = (int)((P.N + 127) / 128);
   S.ncl = ncl;

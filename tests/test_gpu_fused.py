@@ -233,3 +233,37 @@ def test_floor_matches_the_constrained_update(lib):
     Wg, Hg = W.double().cpu().numpy(), H.double().cpu().numpy()
     assert rel(Wg, Wo) < 2 * TOL_WH and rel(Hg, Ho) < 2 * TOL_WH
     m.close()
+
+
+@pytest.mark.parametrize("beta,shape", [(0.0, (300, 700, 20)), (1.5, (200, 333, 12)), (1.0, (129, 500, 32))])
+def test_fused_adjoint_matches_oracle(lib, beta, shape):
+    """nmf_grad on a BF16 context: the fused sweep's adjoint mode (grad_H =
+    W^T (B - A), grad_W = (B - A) H^T from one read of V) against the oracle's
+    gradient; each gradient is a difference of two bf16 contractions, so the
+    bar is 3e-2 of the larger of the two terms' scale, taken as max |grad| of
+    the oracle plus the mean absolute MU numerator (P or Hn) of the oracle."""
+    import torch
+    from paper_2106_15214_gb300.binding import NMF
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=F + K)
+    m = NMF(F, N, K, beta, precision="bf16", order="H")
+    W = torch.tensor(W0, dtype=torch.float32, device="cuda")
+    H = torch.tensor(H0, dtype=torch.float32, device="cuda")
+    m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
+    m.set_factors(W, H)
+    gW, gH = torch.empty_like(W), torch.empty_like(H)
+    loss = m.grad(gW, gH, want_loss=True)
+    oW, oH = O.gradients(V, W0, H0, beta)
+    Vt = W0 @ H0
+    A = V * Vt ** (beta - 2.0)
+    for g, o, num in ((gW, oW, A @ H0.T), (gH, oH, W0.T @ A)):
+        scale = np.max(np.abs(o)) + np.mean(np.abs(num))
+        assert np.max(np.abs(g.double().cpu().numpy() - o)) < 3e-2 * scale
+    assert loss == pytest.approx(O.D_beta(V, Vt, beta), rel=TOL_D)
+    assert torch.equal(W, torch.tensor(W0, dtype=torch.float32, device="cuda"))    # factors untouched
+    assert torch.equal(H, torch.tensor(H0, dtype=torch.float32, device="cuda"))
+    # a step after the gradient (the copies it left are of the same W, H)
+    m.step_joint(1)
+    Wo, Ho, _ = oracle_h_first(V, W0, H0, beta)
+    assert rel(W.double().cpu().numpy(), Wo) < TOL_WH and rel(H.double().cpu().numpy(), Ho) < TOL_WH
+    m.close()
