@@ -345,19 +345,21 @@ _beta_divergence_fn = None
 _grad_contexts = {}
 
 
-def _grad_context(F, N, K, beta, kappa, dtype, device):
-    """A context per (shape, beta, kappa, dtype, device, stream), kept for reuse
-    by the autograd function (contexts own device scratch: creating one per
-    call would allocate every time)."""
+def _grad_context(F, N, K, beta, kappa, dtype, device, fused=False):
+    """A context per (shape, beta, kappa, precision, device, stream), kept for
+    reuse by the autograd function (contexts own device scratch: creating one
+    per call would allocate every time). fused (float32 only): a BF16 context,
+    whose nmf_grad is the fused single-read sweep's adjoint mode."""
     import torch
-    prec = "fp64" if dtype == torch.float64 else "fp32"
+    prec = "fp64" if dtype == torch.float64 else ("bf16" if fused else "fp32")
     stream = torch.cuda.current_stream(device).cuda_stream
     key = (F, N, K, float(beta), float(kappa), prec, device.index, stream)
     m = _grad_contexts.get(key)
     if m is None:
         if len(_grad_contexts) >= 16:
             _grad_contexts.pop(next(iter(_grad_contexts))).close()
-        m = NMF(F, N, K, float(beta), precision=prec, normalize=False, kappa=float(kappa), stream=stream)
+        m = NMF(F, N, K, float(beta), precision=prec, order="H" if prec == "bf16" else "W", normalize=False,
+                kappa=float(kappa), stream=stream)
         _grad_contexts[key] = m
     return m
 
@@ -380,7 +382,7 @@ def _beta_divergence_function():
         differentiated. Contexts are cached per shape and reused."""
 
         @staticmethod
-        def forward(ctx, V, W, H, beta, kappa):
+        def forward(ctx, V, W, H, beta, kappa, fused):
             F, K = W.shape
             N = H.shape[1]
             Vc, Wc, Hc = V.detach().contiguous(), W.detach().contiguous(), H.detach().contiguous()
@@ -392,7 +394,7 @@ def _beta_divergence_function():
                 m.set_factors(Wc, Hc)
                 loss = torch.tensor(m.loss(), dtype=W.dtype, device=W.device)
             ctx.save_for_backward(Vc, Wc, Hc)
-            ctx.beta, ctx.kappa = float(beta), float(kappa)
+            ctx.beta, ctx.kappa, ctx.fused = float(beta), float(kappa), bool(fused) and W.dtype == torch.float32
             return loss
 
         @staticmethod
@@ -400,19 +402,22 @@ def _beta_divergence_function():
             Vc, Wc, Hc = ctx.saved_tensors
             F, K = Wc.shape
             N = Hc.shape[1]
-            m = _grad_context(F, N, K, ctx.beta, ctx.kappa, Wc.dtype, Wc.device)
+            m = _grad_context(F, N, K, ctx.beta, ctx.kappa, Wc.dtype, Wc.device, ctx.fused)
             m.set_dense(Vc)
             m.set_factors(Wc, Hc)
             gW, gH = torch.empty_like(Wc), torch.empty_like(Hc)
             m.grad(gW, gH)                 # asynchronous: no host round trip
-            return None, g * gW, g * gH, None, None
+            return None, g * gW, g * gH, None, None, None
 
     _beta_divergence_fn = BetaDivergence
     return BetaDivergence
 
 
-def beta_divergence(V, W, H, beta, kappa=0.0):
+def beta_divergence(V, W, H, beta, kappa=0.0, fused=False):
     """Differentiable D_beta(V + kappa | WH + kappa) of CUDA tensors V (F x N),
     W (F x K), H (K x N), float32 or float64; backward gives grad_W, grad_H
-    (nmf_grad). Returns a 0-d tensor on W's device."""
-    return _beta_divergence_function().apply(V, W, H, beta, kappa)
+    (nmf_grad). fused=True (float32): the gradients come from the fused
+    single-read sweep's adjoint mode (bf16 contractions, ~1e-2 relative error
+    of each term; K <= 32, F <= 1024, else the FP32 sweeps). Returns a 0-d
+    tensor on W's device."""
+    return _beta_divergence_function().apply(V, W, H, beta, kappa, fused)
