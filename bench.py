@@ -250,6 +250,9 @@ def algorithmic_bytes(kernel, F, N, K, esize=4, order="W"):
         "normalize": 2 * (FK + KN),
         # W, H in; W, H (normalised) out; the next iteration's W~, H~ are the same values
         "normalize_next": 2 * (FK + KN),
+        # the W half after the fused sweep, then the normalisation: P, Q and
+        # W~ in, W out; W, H in, W, H (normalised) out
+        "fused_post": 4 * FK + 2 * (FK + KN),
     }
     return table.get(kernel)
 

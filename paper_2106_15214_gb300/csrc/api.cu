@@ -798,11 +798,11 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
   }
   // NMF_BF16: the fused single-read H-first iteration (tc_fused.cu): the
   // fused sweep (product, A, B, objective, H update, both contractions; H
-  // written) | W update from its partial slices (column norms and the
-  // objective finalised by its last block) | normalisation fused with the
-  // next iteration's copies of W~, H~. The copies of the first iteration come
-  // from the previous call's last kernel while nothing changed W and H in
-  // between (copiesValid), else from the copies kernel.
+  // written) | the W update from its partial slices with the column-norm
+  // partials | the norms, the normalisation, the next iteration's copies of
+  // W~, H~ and the objective. The copies of the first iteration come from
+  // the previous call's last kernel while nothing changed W and H in between
+  // (copiesValid), else from the copies kernel.
   if constexpr (std::is_same<T, float>::value) {
     if (c->prec == NMF_BF16 && c->batched) {
       // many problems: every iteration's copies of all W~, H~ | the fused
@@ -840,6 +840,11 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
       const Prob<float>& P0 = c->hpf[0];
       const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
       const bool haveCopies = copiesIn;
+      // the W half and the normalisation over every SM, the second launch
+      // started early (NMF_FU_POST=0: the W epilogue kernel with its
+      // last-block finalisation, then the normalisation with the next copies)
+      const char* postEnvS = std::getenv("NMF_FU_POST");
+      const bool postOne = !(postEnvS && std::atoi(postEnvS) == 0);
       for (int it = 0; it < iters; ++it) {
         const bool lossHere = wantLoss && it == iters - 1;
         if (it == 0 && !haveCopies)
@@ -848,6 +853,13 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
         NMF_CU(timed(&c->timer, st, "tc_fused", 1, [&] {
           return launch_tc_fused(P0, c->tcmaps, bp, ncl, lp, status, c->waitLimitNs, c->extraArrivals, st);
         }));
+        if (postOne) {
+          NMF_CU(timed(&c->timer, st, "fused_post", 2, [&] {
+            return launch_fused_post(P0, bp, ncl, norm, reinterpret_cast<float*>(c->d_normPart), c->sms, lp, cgrid,
+                                     lossHere ? c->d_lossOut : nullptr, status, st);
+          }));
+          continue;
+        }
         EpiFuse f;
         f.flags = (lossHere ? FUSE_LOSS : 0) | (norm ? FUSE_NORM_PART : 0);
         f.lossPart = lp;

@@ -332,6 +332,15 @@ int tc_fused_clusters(const Prob<float>& P, int sms);
 // gH not null: the adjoint instead of the update (H untouched): grad_H = W~^T (B - A)
 // into gH, and slices of P = A H~^T, Q = B H~^T (grad_W = Q - P by the W epilogue's
 // EPI_GRAD mode).
+// The W half of a fused single-problem iteration and the normalisation
+// (tc_fused.cu), two launches of nparts blocks: the slices' sum and the W update
+// (in place, base W), per-block column sums of squares into normPart (K x
+// nparts floats); then the column norms, W /= norms with its TF32 row copy,
+// H *= norms with Ht and its transposed TF32 copy, and the objective from the
+// sweep's partials (lossOut not null).
+cudaError_t launch_fused_post(const Prob<float>& P, const BetaParams& bp, int slices, bool norm, float* normPart,
+                              int nparts, const double* lossPart, int lossBlocks, double* lossOut, int* status,
+                              cudaStream_t st);
 cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaParams& bp, int ncl, double* lossPart,
                             int* status, uint64_t limitNs, unsigned extra, cudaStream_t st, float* gH = nullptr);
 // The same sweep over many problems in one launch (batched contexts): work

@@ -49,6 +49,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -281,10 +282,12 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
   __syncwarp();
   pdl_wait();
   // W~^T (bf16, the B operand of the H contraction) from the full-precision
-  // W~; chi slots zeroed (their padded rows k >= K stay zero)
+  // W~ (= W at entry: every path leaves Wt equal to W before this launch, and
+  // the W half after a single-problem sweep takes its base from W); chi slots
+  // zeroed (their padded rows k >= K stay zero)
   for (int i = tid; i < 128 * kp; i += FU_THREADS) {
     const int k = i / 128, f = i - k * 128;
-    const float w = (k < K && m0 + f < P.F) ? P.Wt[(m0 + f) * K + k] : 0.f;
+    const float w = (k < K && m0 + f < P.F) ? P.W[(m0 + f) * K + k] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(w);
     *reinterpret_cast<__nv_bfloat16*>(base + L.wb + (f >> 6) * (kp * 128) + sw_bf16(k, f & 63)) = h;
   }
@@ -757,9 +760,318 @@ fused_batch_copies_kernel(const Prob<float>* __restrict__ probs, int count, cons
   }
 }
 
+// ---- the W half of the iteration and the normalisation ---------------------
+//
+// After the fused sweep the W update needs the sum of the clusters' partial
+// slices of [P | Q] (2 x slices x F x K floats, resident in L2), and the
+// normalisation of Sec. 4.1.2 needs the column norms of the whole new W before
+// any entry of W or H can be scaled. Two launches, each spread over every SM:
+//   fused_w_kernel     the slice sums and the W update of this block's share
+//                      of the entries (the new W written in place: each entry
+//                      is read as the base W~ and rewritten by one thread), and
+//                      the block's per-column sums of squares;
+//   fused_norm_kernel  launched early (programmatic dependent launch): it loads
+//                      its columns of H (final since the fused sweep) before
+//                      waiting for fused_w_kernel; then every block sums the
+//                      column partials in the same fixed order (the same norms
+//                      in every block), divides its share of W by them (with
+//                      the TF32 row copy), scales its columns of H (H, Ht, the
+//                      transposed TF32 copy), and block 0 sums the objective.
+constexpr int POST_THREADS = 512;    // both kernels; two blocks per SM (one of each), <= 64 registers
+constexpr int POST_CH = 256;         // columns of H per pass through shared memory
+constexpr int POST_DEPTH = 4;        // slices per lane with loads in flight together
+// fused_w_kernel: lane partials of P and Q (2 x POST_THREADS float4), the W~ quads, then the squares
+constexpr size_t POSTW_SMEM = 3 * POST_THREADS * sizeof(float4);
+// fused_norm_kernel: the H tile (POST_CH x (K + 1) floats, K <= 32), then its
+// rows in the layout of the transposed TF32 copy (POST_CH x 32 floats)
+constexpr size_t POSTN_SMEM = (size_t)POST_CH * 33 * sizeof(float) + (size_t)POST_CH * 32 * sizeof(float);
+
+struct PostParams {
+  int slices;               // partial slices of [P | Q] (the fused sweep's clusters)
+  int norm;                 // normalise (Sec. 4.1.2)
+  float* normPart;          // [K][gridDim of fused_w_kernel] sums of squares
+  const double* lossPart;   // the fused sweep's objective partials
+  int lossBlocks;
+  double* lossOut;          // null: the objective is not wanted
+  int* status;
+};
+
+// Four consecutive entries from e (the entries past FK read as zero).
+__device__ __forceinline__ float4 post_ld4(const float* p, int e, int FK, bool vec) {
+  if (vec) return *reinterpret_cast<const float4*>(p + e);
+  float4 v;
+  v.x = e < FK ? p[e] : 0.f;
+  v.y = e + 1 < FK ? p[e + 1] : 0.f;
+  v.z = e + 2 < FK ? p[e + 2] : 0.f;
+  v.w = e + 3 < FK ? p[e + 3] : 0.f;
+  return v;
+}
+__device__ __forceinline__ void add4(float4& a, const float4& b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
+}
+__device__ __forceinline__ float get4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+template <int BK, bool VEC>
+__global__ void __launch_bounds__(POST_THREADS, 2)
+fused_w_kernel(Prob<float> P, BetaParams bp, PostParams Q) {
+  extern __shared__ float4 post_sm[];
+  float4* redN = post_sm;                                   // [G][nq] lane partials of P
+  float4* redD = post_sm + POST_THREADS;                    // and of Q
+  float4* base4 = post_sm + 2 * POST_THREADS;               // W~ of quad tid, then its squares
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = (int)blockIdx.x, nb = (int)gridDim.x;
+  pdl_wait();
+  pdl_trigger();         // after the wait: the next kernel reads H before its own wait
+  const bool skip = *Q.status != 0;
+  const int K = P.K;
+  const int FK = (int)(P.F * K), NQ = (FK + 3) / 4;          // F K <= 32768: 32-bit entry indices
+  const int qa = (int)((int64_t)NQ * b / nb), qb = (int)((int64_t)NQ * (b + 1) / nb);
+  const int nq = qb - qa;                                    // this block's quads of entries (<= POST_THREADS)
+  const int G = nq > 0 ? max(1, min(Q.slices, POST_THREADS / nq)) : 1;   // lanes per quad
+  constexpr bool vec = VEC;            // F K a multiple of 4: 16-byte loads of whole quads
+  if (tid < nq) {
+    const int e0 = 4 * (qa + tid);
+    if (vec) {
+      cp_async16(&base4[tid], P.W + e0);
+    } else {
+      float* bs = reinterpret_cast<float*>(&base4[tid]);
+      for (int i = 0; i < 4; ++i) cp_async4(bs + i, e0 + i < FK ? P.W + e0 + i : P.W, e0 + i < FK ? 4u : 0u);
+    }
+  }
+  // P and Q of the block's entries: lane g of a quad sums slices g, g + G, ...
+  // in order, then the G lanes in order
+  if (tid < G * nq) {
+    const int q = tid % nq, g = tid / nq;
+    const int e0 = 4 * (qa + q);
+    float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = n4;
+    const int step = 2 * FK * G;                   // floats from one of this lane's slices to its next
+    const float* part = P.rowPart + (int64_t)g * 2 * FK;
+    for (int s0 = g; s0 < Q.slices; s0 += POST_DEPTH * G, part += POST_DEPTH * step) {
+      float4 vn[POST_DEPTH], vd[POST_DEPTH];
+      #pragma unroll
+      for (int u = 0; u < POST_DEPTH; ++u) {
+        const bool in = s0 + u * G < Q.slices;
+        vn[u] = in ? post_ld4(part + u * step, e0, FK, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vd[u] = in ? post_ld4(part + u * step + FK, e0, FK, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      #pragma unroll
+      for (int u = 0; u < POST_DEPTH; ++u) {
+        add4(n4, vn[u]);
+        add4(d4, vd[u]);
+      }
+    }
+    redN[g * nq + q] = n4;
+    redD[g * nq + q] = d4;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // the W update of eq. jnt_update (W half, base W~), written in place
+  float* sq = reinterpret_cast<float*>(base4);
+  if (tid < nq) {
+    const float4 base = base4[tid];
+    float4 n4 = redN[tid], d4 = redD[tid];
+    for (int g = 1; g < G; ++g) {
+      add4(n4, redN[g * nq + tid]);
+      add4(d4, redD[g * nq + tid]);
+    }
+    const int e0 = 4 * (qa + tid);
+    float x[4];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = 0.f;
+      if (e0 + i < FK) {
+        x[i] = apply_floor(get4(base, i) * mu_ratio<BK, float>(get4(n4, i), get4(d4, i), (float)bp.gamma),
+                           (float)bp.floor);
+        if (!skip) {
+          if (!isfinite(x[i])) atomicExch(Q.status, 4);
+          P.W[e0 + i] = x[i];
+        }
+      }
+    }
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) sq[4 * tid + i] = x[i] * x[i];   // (the thread's own W~ quad, read above)
+  }
+  __syncthreads();
+  // per-column sums of squares over the block's entries: warp w takes columns
+  // w, w + 16, ...; its lanes every 32nd entry of the column in order, then a
+  // fixed butterfly
+  const int jn = min(4 * nq, FK - 4 * qa);
+  for (int k = warp; k < K; k += POST_THREADS / 32) {
+    const int j0 = ((k - (4 * qa) % K) % K + K) % K;
+    float acc = 0.f;
+    for (int j = j0 + K * lane; j < jn; j += 32 * K) acc += sq[j];
+    acc = warp_sum(acc);
+    if (lane == 0) Q.normPart[(int64_t)k * nb + b] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(POST_THREADS, 2)
+fused_norm_kernel(Prob<float> P, PostParams Q, int nparts) {
+  extern __shared__ float4 post_sm[];
+  float* tile = reinterpret_cast<float*>(post_sm);
+  float* rows = tile + POST_CH * 33;                 // 16-byte aligned (POST_CH * 33 * 4 bytes)
+  __shared__ float s_norm[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = (int)blockIdx.x, nb = (int)gridDim.x;
+  const int K = P.K, K1 = P.K + 1;
+  // this block's columns of H; the first pass is loaded before the wait (H is
+  // final since the fused sweep, which completed before fused_w_kernel let this
+  // launch start). Units of 32 consecutive columns of one row k: warp w takes
+  // units w, w + 16, ... (lane = column), no division per entry.
+  const int64_t n_lo = P.N * b / nb, n_hi = P.N * (b + 1) / nb;
+  auto load_h = [&](int64_t c0, int len) {
+    const int ng = (len + 31) >> 5;
+    for (int u = warp; u < K * ng; u += POST_THREADS / 32) {
+      const int k = u / ng, nl = ((u - k * ng) << 5) + lane;
+      if (nl < len) cp_async4(&tile[nl * K1 + k], P.H + (int64_t)k * P.N + c0 + nl, 4u);
+    }
+  };
+  if (n_lo < n_hi) load_h(n_lo, (int)min((int64_t)POST_CH, n_hi - n_lo));
+  pdl_wait();
+  const bool skip = *Q.status != 0;
+  if (Q.lossOut && b == 0 && warp == POST_THREADS / 32 - 1) {
+    // the objective of the sweep: its block partials in a fixed order, FP64
+    double sl = 0.0;
+    for (int b0 = lane; b0 < Q.lossBlocks; b0 += 256) {
+      double v[8];
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = b0 + 32 * u < Q.lossBlocks ? Q.lossPart[b0 + 32 * u] : 0.0;
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) sl += v[u];
+    }
+    sl = warp_sum(sl);
+    if (lane == 0) Q.lossOut[0] = sl;
+  }
+  // column norms: 16 lanes per column (thread (k, j) sums the partials j,
+  // j + 16, ... in order), one fixed butterfly over the 16: the same value in
+  // every block
+  {
+    const int k = tid >> 4, j = tid & 15;
+    float acc = 0.f;
+    if (k < K)
+      for (int i = j; i < nparts; i += 16) acc += Q.normPart[(int64_t)k * nparts + i];
+    #pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (k < K && j == 0) s_norm[k] = Q.norm ? sqrtf(acc) : 1.f;
+  }
+  __syncthreads();
+  // this block's share of W: W /= norms, with the TF32 row copy
+  const int FK = (int)(P.F * K);
+  const int e_lo = (int)((int64_t)FK * b / nb), e_hi = (int)((int64_t)FK * (b + 1) / nb);
+  if (!skip)
+    for (int e = e_lo + tid; e < e_hi; e += POST_THREADS) {
+      const int f = e / K, k = e - f * K;
+      const float nk = s_norm[k];
+      float w = P.W[e];
+      if (nk > 0.f) w = w / nk;
+      P.W[e] = w;
+      P.sWS[f * P.ks + k] = tf32_round(w);
+    }
+  if (b == 0 && tid < K && !skip) P.norms[tid] = s_norm[tid];
+  // H[k, :] *= norm_k over this block's columns, with Ht and the transposed
+  // TF32 copy: its rows (ks = 32 floats; the padding k >= K written as the
+  // zeros it holds) for columns [c0, c0 + len) are contiguous, built in shared
+  // memory and written with one bulk copy
+  for (int64_t c0 = n_lo; c0 < n_hi; c0 += POST_CH) {
+    const int len = (int)min((int64_t)POST_CH, n_hi - c0);
+    if (c0 != n_lo) {
+      if (tid == 0) bulk_wait_read();          // the previous pass's rows were read out
+      __syncthreads();
+      load_h(c0, len);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int ng = (len + 31) >> 5;
+    for (int u = warp; u < K * ng; u += POST_THREADS / 32) {
+      const int k = u / ng, nl = ((u - k * ng) << 5) + lane;
+      if (nl < len) {
+        float h = tile[nl * K1 + k];
+        const float nk = s_norm[k];
+        if (nk > 0.f) h = h * nk;
+        if (!skip) {
+          P.H[(int64_t)k * P.N + c0 + nl] = h;
+          P.Ht[(int64_t)k * P.N + c0 + nl] = h;
+        }
+        tile[nl * K1 + k] = tf32_round(h);
+      }
+    }
+    __syncthreads();
+    for (int nl = warp; nl < len; nl += POST_THREADS / 32) rows[nl * 32 + lane] = lane < K ? tile[nl * K1 + lane] : 0.f;
+    fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0 && !skip) {
+      bulk_store(P.sHT + c0 * 32, rows, (uint32_t)len * 128u);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait_read();
+}
+
 }  // namespace
 
 // ---- host ------------------------------------------------------------------
+
+// The W half and the normalisation after a fused single-problem sweep: two
+// launches over every SM, the second with programmatic dependent launch (its
+// blocks sit beside the first's: two blocks per SM).
+namespace {
+template <typename KernelT>
+cudaError_t post_smem_once(KernelT kern, size_t bytes) {
+  return ensure_smem_attr(reinterpret_cast<const void*>(kern), bytes);
+}
+}  // namespace
+
+cudaError_t launch_fused_post(const Prob<float>& P, const BetaParams& bp, int slices, bool norm, float* normPart,
+                              int nparts, const double* lossPart, int lossBlocks, double* lossOut, int* status,
+                              cudaStream_t st) {
+  const int64_t FK = P.F * P.K;
+  // every block of the first launch takes at most POST_THREADS quads of entries
+  // (the transposed copy's rows are 32 floats: ks = 32 for K <= 32)
+  if (P.K > 32 || P.ks != 32 || slices < 1 || nparts < 1 || (FK + 3) / 4 > (int64_t)POST_THREADS * nparts ||
+      FK > 32768)
+    return cudaErrorInvalidValue;
+  PostParams Q;
+  Q.slices = slices;
+  Q.norm = norm ? 1 : 0;
+  Q.normPart = normPart;
+  Q.lossPart = lossPart;
+  Q.lossBlocks = lossBlocks;
+  Q.lossOut = lossOut;
+  Q.status = status;
+  const bool vec = FK % 4 == 0;
+  cudaError_t e = cudaSuccess;
+#define NMF_POSTW_CASE(BKV)                                                                               \
+  case BKV:                                                                                               \
+    if (vec) {                                                                                            \
+      e = post_smem_once(fused_w_kernel<BKV, true>, POSTW_SMEM);                                          \
+      if (e == cudaSuccess)                                                                               \
+        e = launch_pdl(fused_w_kernel<BKV, true>, dim3(nparts), dim3(POST_THREADS), POSTW_SMEM, st, P, bp, Q); \
+    } else {                                                                                              \
+      e = post_smem_once(fused_w_kernel<BKV, false>, POSTW_SMEM);                                         \
+      if (e == cudaSuccess)                                                                               \
+        e = launch_pdl(fused_w_kernel<BKV, false>, dim3(nparts), dim3(POST_THREADS), POSTW_SMEM, st, P, bp, Q); \
+    }                                                                                                     \
+    break;
+  switch (bp.kind) {
+    NMF_POSTW_CASE(BK_IS)
+    NMF_POSTW_CASE(BK_KL)
+    NMF_POSTW_CASE(BK_EUC)
+    NMF_POSTW_CASE(BK_B15)
+    NMF_POSTW_CASE(BK_GENERAL)
+  }
+#undef NMF_POSTW_CASE
+  if (e != cudaSuccess) return e;
+  e = post_smem_once(fused_norm_kernel, POSTN_SMEM);
+  if (e == cudaSuccess)
+    e = launch_pdl(fused_norm_kernel, dim3(nparts), dim3(POST_THREADS), POSTN_SMEM, st, P, Q, nparts);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fused_batch_copies(const Plan<float>& pl, const int* prefHc, int totHc, const int* status,
                                       cudaStream_t st) {

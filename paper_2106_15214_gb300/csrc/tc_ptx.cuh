@@ -169,6 +169,22 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc, uint
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
                :: "r"(smem_u32(smem_dst)), "l"(gsrc), "r"(src_bytes) : "memory");
 }
+// 16-byte cp.async global -> shared (both addresses 16-byte aligned), L2 only.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+// Bulk copy shared -> global of `bytes` contiguous bytes (both addresses
+// 16-byte aligned, bytes a multiple of 16), tracked as a bulk group of the
+// issuing thread.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               :: "l"(gdst), "r"(smem_u32(smem_src)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the issuing thread's bulk copies have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until all of this thread's earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Arrives on the mbarrier once all of this thread's earlier cp.async copies have
 // landed; counts as one of the barrier's expected arrivals (.noinc).
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* m) {
@@ -207,6 +223,19 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
+// Blocks in this block's cluster.
+__device__ __forceinline__ uint32_t cluster_nblocks() {
+  uint32_t n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+// The two halves of cluster_sync, for work between the arrival and the wait.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+// Arrival without release semantics (the caller orders what must be seen first).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
 // Address of the same shared-memory location in block `rank` of the cluster.
 __device__ __forceinline__ uint32_t dsmem_map(const void* local, uint32_t rank) {
   uint32_t r;
@@ -243,6 +272,11 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* m, uint32_t pari
       "selp.b32 %0, 1, 0, p;\n\t}"
       : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ float dsmem_ld1(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
 }
 __device__ __forceinline__ float4 dsmem_ld4(uint32_t addr) {
   float4 v;

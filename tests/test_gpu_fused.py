@@ -68,6 +68,33 @@ def test_one_iteration_matches_oracle(lib, shape, beta):
     assert loss == pytest.approx(lo[0], rel=TOL_D)
 
 
+@pytest.mark.parametrize("shape,beta", [((101, 301, 5), 1.0), ((130, 40000, 8), 0.0), ((1024, 700, 32), 1.5)])
+def test_w_half_launch_shapes(lib, shape, beta):
+    """The launch after the fused sweep (every cluster sums all the partial
+    slices; column norms combined over distributed shared memory; W and H
+    normalised with their next copies) on F K not a multiple of 4 (no 16-byte
+    loads), more columns of H per block than one pass through shared memory,
+    and the largest F and K: two iterations (the second from the copies the
+    first left) against the oracle; one iteration against the separate W
+    epilogue and normalisation kernels (NMF_FU_POST=0), which differ only in
+    the order of the slice sums (the objective, from the same sweep, equal)."""
+    import os
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=F * 3 + K)
+    W, H, loss = run_bf16(V, W0, H0, beta, iters=2)
+    Wo, Ho, lo = oracle_h_first(V, W0, H0, beta, iters=2)
+    assert rel(W, Wo) < 2 * TOL_WH and rel(H, Ho) < 2 * TOL_WH
+    assert loss == pytest.approx(lo[1], rel=TOL_D)
+    W1, H1, loss1 = run_bf16(V, W0, H0, beta)
+    os.environ["NMF_FU_POST"] = "0"
+    try:
+        W2, H2, loss2 = run_bf16(V, W0, H0, beta)
+    finally:
+        del os.environ["NMF_FU_POST"]
+    assert rel(W1, W2) < 1e-5 and rel(H1, H2) < 1e-5
+    assert loss1 == loss2
+
+
 @pytest.mark.parametrize("beta", [-1.0, 0.5, 3.0])
 def test_general_beta(lib, beta):
     V, W0, H0 = problem(300, 400, 16, seed=5)
