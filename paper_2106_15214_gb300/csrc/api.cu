@@ -838,7 +838,7 @@ nmf_status run_dense(nmf_ctx* c, Plan<T>& pl, bool joint, int iters, bool wantLo
     }
     if (c->prec == NMF_BF16) {
       const Prob<float>& P0 = c->hpf[0];
-      const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
+      const int ncl = P0.fuS, cgrid = tc_fused_cluster_blocks(P0) * ncl;
       const bool haveCopies = copiesIn;
       // the W half and the normalisation over every SM, the second launch
       // started early (NMF_FU_POST=0: the W epilogue kernel with its
@@ -1434,7 +1434,7 @@ nmf_status nmf_grad(nmf_ctx* c, void* gW_dev, void* gH_dev, double* loss_out) {
     if (s == NMF_OK && c->tcmaps.ok && tc_fused_supported(c->hpf[0])) {
       const Prob<float>& P0 = c->hpf[0];
       const BetaParams bp = beta_params(c);
-      const int ncl = P0.fuS, cgrid = (int)((P0.F + 127) / 128) * ncl;
+      const int ncl = P0.fuS, cgrid = tc_fused_cluster_blocks(P0) * ncl;
       const bool wantLoss = loss_out != nullptr;
       int* status = c->d_status;
       double* lp = c->d_lossPart;

@@ -325,6 +325,9 @@ cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, in
 // contractions, TF32 product): K <= 32, F <= 1024. It writes H (before the
 // normalisation), one [P | Q] partial slice per cluster into rowPart (ncl
 // slices) and one objective partial per block (grid = ceil(F / 128) x ncl).
+// Blocks per cluster of the single-problem fused sweep (ceil(F / 128), or
+// F / 128 when the last block also takes 1 or 2 tail rows).
+int tc_fused_cluster_blocks(const Prob<float>& P);
 bool tc_fused_supported(const Prob<float>& P);
 // Clusters of ceil(F / 128) blocks that can be resident at once (at most the
 // number of 128-column batches); 0 when the kernel cannot launch.

@@ -7,9 +7,12 @@
 //   H = Ht . ((Wt^T A) / (Wt^T B))^gamma            (reduction over f)
 //   W = Wt . ((A chi_1(H, Ht)^T) / (B chi_2(H, Ht)^T))^gamma  (reduction over n)
 //
-// Work split. A cluster of c = ceil(F / 128) blocks owns a run of 128-column
-// batches of V; block r of the cluster owns rows [128 r, 128 r + 128) (the
-// TMEM lanes of its tiles). Per batch each block
+// Work split. A cluster of c blocks owns a run of 128-column batches of V;
+// block r of the cluster owns rows [128 r, 128 r + 128) (the TMEM lanes of its
+// tiles). c = ceil(F / 128), except when F = 128 c + t with 1 <= t <= 2 (a
+// spectrogram's F = 2^m + 1 frequency bins): then the last block's warp 0 also
+// takes the t rows past its 128 in FP32, so that one block per cluster less
+// is needed (more clusters fit on the GPU). Per batch each block
 //   1. forms Vt (128 x 128, tcgen05 kind::tf32, W~ rows in TMEM, H~^T rows in
 //      shared memory) and, tile by tile (32 columns), reads V, evaluates A, B
 //      and the objective in registers (FP32; FP64 below the small-Vt guard),
@@ -27,13 +30,14 @@
 //      its W numerator and denominator (TMEM, accumulated over the batches).
 // At the end every block writes its [P | Q] rows as one partial slice (one per
 // cluster); the W epilogue kernel sums the slices in fixed order. The next
-// batch's product and epilogue overlap the exchange: two TMEM batch buffers,
-// two H-accumulator slots and two chi slots alternate.
+// batch's product and epilogue overlap the exchange: three TMEM batch buffers,
+// two H~^T slots and two chi slots alternate.
 //
-// Roles (24 warps): 0 operand loads (W~ rows once, H~^T rows per batch), 1 V
-// tiles, 2 MMA issue, 3 idle, 4-19 epilogue (two groups of 8 warps on
-// alternate tiles, each thread one TMEM lane and 16 columns of a tile), 20-23
-// the exchange (one TMEM lane quarter each). Every wait is bounded (1 s, then
+// Roles (24 warps): 0 operand loads (W~ rows once, H~^T rows per batch) and
+// the tail rows, 1 V tiles, 2 MMA issue, 4-19 epilogue (two groups of 8 warps
+// on alternate tiles, each thread one TMEM lane and 16 columns of a tile),
+// 20-23 and 3 the exchange (20-23 read one TMEM lane quarter each; all five
+// reduce). Every wait is bounded (1 s, then
 // NMF_ETIMEOUT and every role leaves its loop); the blocks of a cluster meet
 // only in bounded mbarrier waits, plus one cluster barrier at entry and one at
 // exit that every block reaches.
@@ -62,6 +66,13 @@ namespace {
 constexpr int FU_THREADS = 768;
 constexpr int FU_EPI0 = 4;           // first epilogue warp
 constexpr int FU_EX0 = 20;           // first exchange warp
+// exchange warps: 20-23 read the H accumulator (one TMEM lane quarter each)
+// and reduce; with tail rows (clusters of F / 128 blocks, 25 % more tasks a
+// block) warp 3 reduces too
+constexpr int FU_TAIL_MAX = 2;       // rows past the last block's 128 handled in FP32 by warp 0 (F = 128 c + tail)
+constexpr size_t FU_STATIC_RESERVE = 1024;   // the kernel's static shared memory (barriers)
+// tail-row buffers: W~ rows [FU_TAIL_MAX][32], then A, B per slot [2][FU_TAIL_MAX][2][128] (floats)
+constexpr uint32_t FU_TAIL_BYTES = 4u * (FU_TAIL_MAX * 32 + 2 * FU_TAIL_MAX * 2 * 128);
 constexpr int FU_MAXV = 6;
 constexpr int FU_ETIMEOUT = 5;
 constexpr uint32_t FU_TB = 16384;    // one V tile (128 x 32 floats) or one H~^T batch (128 x 32)
@@ -80,6 +91,7 @@ struct FuLayout {
   uint32_t chi0;     // 2 chi slots: chi_1 then chi_2, each 2 K-atoms (64 columns n) x kp rows x 128 B
   uint32_t chiSlot;
   uint32_t mb;       // mailbox: 2K rows (Hn then Hd) x 128 floats
+  uint32_t tail;     // tail-row buffers (FU_TAIL_BYTES)
   uint32_t total;
   int nv;
 };
@@ -95,7 +107,8 @@ __host__ __device__ inline FuLayout fu_layout(int K, int kp, int nv) {
   L.chi0 = L.wb + 2u * (uint32_t)kp * 128u;
   L.chiSlot = 4u * (uint32_t)kp * 128u;
   L.mb = L.chi0 + 2u * L.chiSlot;
-  L.total = L.mb + 2u * (uint32_t)K * 512u;
+  L.tail = L.mb + 2u * (uint32_t)K * 512u;
+  L.total = L.tail + FU_TAIL_BYTES;
   L.nv = nv;
   return L;
 }
@@ -103,7 +116,7 @@ __host__ __device__ inline FuLayout fu_layout(int K, int kp, int nv) {
 // Deepest V ring that fits (at least 2 tiles).
 inline int fu_pick_nv(int K, int kp) {
   for (int nv = FU_MAXV; nv >= 2; --nv)
-    if (1024 + fu_layout(K, kp, nv).total <= FU_SMEM_LIMIT) return nv;
+    if (1024 + fu_layout(K, kp, nv).total + FU_STATIC_RESERVE <= FU_SMEM_LIMIT) return nv;
   return 0;
 }
 
@@ -116,6 +129,9 @@ struct FuBars {
   // j has landed (that one reaches the barrier only through a third block),
   // but its arrival for j + 2 is causally after this block's own wait for j.
   uint64_t mailfull[2], chifull[2];
+  // tail rows (last block): their A, B of batch j are in slot j & 1; warp 0
+  // has read batch j's chi
+  uint64_t tailfull[2], tailfree[2];
 };
 
 struct FuParams {
@@ -130,6 +146,8 @@ struct FuParams {
   unsigned extra;    // arrivals the cluster barriers expect beyond the c blocks (0; 1 in the timeout test)
   int early;         // launched without programmatic dependent launch: the operand copies are complete at
                      // entry, so their first loads go out with the first V tiles
+  int tail;          // F = 128 c + tail, 0 <= tail <= FU_TAIL_MAX: the last block's warp 0 takes the
+                     // rows past its 128 (one problem only)
   float* gH;         // not null: the adjoint instead of the update: the exchange writes
                      // grad_H = W~^T (B - A) here and pushes chi_1 = chi_2 = H~, so the W
                      // contraction gives P = A H~^T, Q = B H~^T (grad_W = Q - P); H is not written
@@ -184,7 +202,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // Byte offset of bf16 element e (0..63) of row r in a 128B-swizzled K-atom.
 __device__ __forceinline__ uint32_t sw_bf16(uint32_t r, uint32_t e) { return sw128_offset(r, 2u * e); }
 
-__device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned extra) {
+__device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, int nex, unsigned extra) {
   for (int s = 0; s < nv; ++s) {
     mbar_init(&B.vfull[s], 1u);
     mbar_init(&B.vempty[s], 8u);           // the 8 warps of the group reading the tile
@@ -198,9 +216,11 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned 
   for (int s = 0; s < 2; ++s) {
     mbar_init(&B.fafull[s], 1u);
     mbar_init(&B.fafree[s], 1u);
-    mbar_init(&B.chiready[s], 4u);
-    mbar_init(&B.mailfull[s], 4u * (uint32_t)c + extra);    // every exchange warp of every block
-    mbar_init(&B.chifull[s], 4u * (uint32_t)c + extra);
+    mbar_init(&B.chiready[s], (uint32_t)nex);
+    mbar_init(&B.mailfull[s], 4u * (uint32_t)c + extra);    // every reading exchange warp of every block
+    mbar_init(&B.chifull[s], (uint32_t)nex * (uint32_t)c + extra);   // every exchange warp of every block
+    mbar_init(&B.tailfull[s], 1u);
+    mbar_init(&B.tailfree[s], 1u);
   }
   mbar_init(&B.stashfull, 32u);            // 4 tiles x 8 warps per batch
   mbar_init(&B.stashfree, 1u);
@@ -209,9 +229,209 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, unsigned 
   fence_mbar_init();
 }
 
+// ---- tail rows (F = 128 c + t, t <= FU_TAIL_MAX): warp 0 of the last block --
+//
+// The rows past the block's 128 TMEM lanes, in FP32 between the warp's H~^T
+// loads. Per batch j, once its H~^T rows are in their slot: the rows' product
+// with H~ (the TF32 values MMA1 reads), A, B and objective terms, four
+// columns per lane, into tail slot j & 1 for the exchange warps, which add the
+// rows' terms to the block's H partials. Once chi of batch j is in: the rows'
+// W numerators and denominators, lane k summing over the batch's columns in
+// order, accumulated over the batches and written into the cluster's slice at
+// the end. A load goes out as soon as its slot is free (MMA1 and these
+// rows done with it); every wait polls the loads and is bounded. Not inlined:
+// its registers stay out of the kernel's hot roles. Returns the loads issued.
+struct FuTail {
+  const float* V;
+  int64_t ldv, N, F;
+  float* rowPart;                 // this cluster's slice [P | Q]
+  int K, kp, row0, tailE, b0, nbr, issued;
+  unsigned char* fa;              // H~^T slots
+  unsigned char* chi;             // chi slots
+  uint32_t chiSlot;
+  const CUtensorMap* tmH;
+  FuBars* bars;
+  const float* wtail;             // [FU_TAIL_MAX][32] W~ rows (zero past the tail and K)
+  float* tab;                     // [2][FU_TAIL_MAX][2][128] A, B per slot
+  volatile int* abort;
+  int* status;
+  uint64_t lim;
+};
+
+template <int BK>
+__device__ __noinline__ int fu_tail_warp(const FuTail& A, const BetaParams& bp, float& lossHi, float& lossLo) {
+  const int lane = threadIdx.x & 31;
+  // the descriptor's fields once, in registers
+  const int K = A.K, kp = A.kp, tailE = A.tailE, nbr = A.nbr, b0 = A.b0, row0 = A.row0;
+  const int64_t N = A.N, ldv = A.ldv, F = A.F;
+  const float* V = A.V;
+  unsigned char* const faB = A.fa;
+  const unsigned char* const chiB = A.chi;
+  const uint32_t chiSlot = A.chiSlot;
+  const float* const wtail = A.wtail;
+  float* const tabB = A.tab;
+  FuBars* const bars = A.bars;
+  const CUtensorMap* const tmH = A.tmH;
+  volatile int* const abort = A.abort;
+  int* const status = A.status;
+  const uint64_t lim = A.lim;
+  float* const rowPart = A.rowPart;
+  auto tab = [&](int s, int e, int ab) -> float* { return tabB + ((s * FU_TAIL_MAX + e) * 2 + ab) * 128; };
+  float pt[FU_TAIL_MAX], qt[FU_TAIL_MAX];
+  #pragma unroll
+  for (int e = 0; e < FU_TAIL_MAX; ++e) pt[e] = qt[e] = 0.f;
+  const float kappa = (float)bp.kappa, bm2 = (float)(bp.beta - 2.0);
+  int issued = A.issued, tb = 0;       // tb: batches whose tail terms are out (their slots' reads done)
+  auto pump = [&]() {
+    while (issued < nbr && issued - 2 < tb &&
+           (issued < 2 ||
+            __all_sync(0xffffffffu, mbar_test(&bars->fafree[issued & 1], (uint32_t)((issued - 2) >> 1) & 1u)))) {
+      const int s = issued & 1;
+      if (elect_one()) {
+        mbar_arrive_expect_tx(&bars->fafull[s], FU_TB);
+        tma_load_2d(faB + s * FU_TB, tmH, 0, (int)(128 * (int64_t)(b0 + issued)), &bars->fafull[s]);
+      }
+      __syncwarp();
+      ++issued;
+    }
+  };
+  auto wait_pump = [&](uint64_t* bar, uint32_t par) -> bool {
+    const uint64_t t0 = globaltimer_ns();
+    while (!__all_sync(0xffffffffu, mbar_test(bar, par))) {
+      pump();
+      if (*abort) return false;
+      if (globaltimer_ns() - t0 > lim) {
+        if (lane == 0) {
+          *abort = 1;
+          atomicExch(status, FU_ETIMEOUT);
+        }
+        __syncwarp();
+        return false;
+      }
+    }
+    return true;
+  };
+  auto tail_ab = [&](int j) {
+    const int s = j & 1;
+    const int64_t nb0 = 128 * (int64_t)(b0 + j);
+    const unsigned char* fa = faB + s * FU_TB;
+    float v[FU_TAIL_MAX][4];                         // V of the rows, issued first (in flight with the product)
+    #pragma unroll
+    for (int e = 0; e < FU_TAIL_MAX; ++e)
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t n = nb0 + lane + 32 * u;
+        v[e][u] = 1.f;
+        if (e < tailE && n < N) v[e][u] = __ldg(&V[(int64_t)(row0 + e) * ldv + n]);
+      }
+    float y[FU_TAIL_MAX][4];
+    #pragma unroll
+    for (int e = 0; e < FU_TAIL_MAX; ++e)
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) y[e][u] = 0.f;
+    for (int k4 = 0; k4 < K; k4 += 4) {                // H~^T rows n, elements k4 .. k4 + 3 (zeros past K)
+      float4 w[FU_TAIL_MAX];
+      #pragma unroll
+      for (int e = 0; e < FU_TAIL_MAX; ++e) w[e] = *reinterpret_cast<const float4*>(wtail + 32 * e + k4);
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 h = *reinterpret_cast<const float4*>(fa + sw128_offset((uint32_t)(lane + 32 * u), 4u * k4));
+        #pragma unroll
+        for (int e = 0; e < FU_TAIL_MAX; ++e) {
+          y[e][u] = fmaf(w[e].x, h.x, y[e][u]);
+          y[e][u] = fmaf(w[e].y, h.y, y[e][u]);
+          y[e][u] = fmaf(w[e].z, h.z, y[e][u]);
+          y[e][u] = fmaf(w[e].w, h.w, y[e][u]);
+        }
+      }
+    }
+    fence_smem_to_async();                             // the slot's reads before its next TMA load
+    __syncwarp();
+    tb = j + 1;
+    pump();
+    float tl = 0.f;
+    #pragma unroll
+    for (int e = 0; e < FU_TAIL_MAX; ++e)
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int nl = lane + 32 * u;
+        float a = 0.f, b = 0.f;
+        if (e < tailE && nb0 + nl < N) epi_terms<BK>(v[e][u] + kappa, y[e][u] + kappa, bm2, bp, true, tl, a, b);
+        tab(s, e, 0)[nl] = a;
+        tab(s, e, 1)[nl] = b;
+      }
+    ff_add(lossHi, lossLo, tl);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars->tailfull[s]);
+  };
+  // the rows' W numerators and denominators over batch j: lane k takes chi
+  // row k, eight columns (one 16-byte chunk) at a time, in column order
+  auto tail_chi = [&](int j) {
+    const int s = j & 1;
+    const unsigned char* chi = chiB + s * chiSlot;
+    if (lane < K) {
+      const uint32_t k = (uint32_t)lane;
+      for (int n0 = 0; n0 < 128; n0 += 8) {
+        const uint32_t off = ((uint32_t)n0 >> 6) * (uint32_t)(kp * 128) + k * 128u +
+                             (((((uint32_t)n0 & 63u) >> 3) ^ (k & 7u)) << 4);
+        const uint4 c1 = *reinterpret_cast<const uint4*>(chi + off);
+        const uint4 c2 = *reinterpret_cast<const uint4*>(chi + off + 2u * (uint32_t)kp * 128u);
+        const uint32_t w1[4] = {c1.x, c1.y, c1.z, c1.w}, w2[4] = {c2.x, c2.y, c2.z, c2.w};
+        #pragma unroll
+        for (int e = 0; e < FU_TAIL_MAX; ++e) {
+          if (e < tailE) {
+            const float4 a0 = *reinterpret_cast<const float4*>(tab(s, e, 0) + n0);
+            const float4 a1 = *reinterpret_cast<const float4*>(tab(s, e, 0) + n0 + 4);
+            const float4 g0 = *reinterpret_cast<const float4*>(tab(s, e, 1) + n0);
+            const float4 g1 = *reinterpret_cast<const float4*>(tab(s, e, 1) + n0 + 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const __nv_bfloat162 h1 = *reinterpret_cast<const __nv_bfloat162*>(&w1[i]);
+              const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w2[i]);
+              const float2 x1 = __bfloat1622float2(h1), x2 = __bfloat1622float2(h2);
+              pt[e] = fmaf(av[2 * i], x1.x, pt[e]);
+              pt[e] = fmaf(av[2 * i + 1], x1.y, pt[e]);
+              qt[e] = fmaf(bv[2 * i], x2.x, qt[e]);
+              qt[e] = fmaf(bv[2 * i + 1], x2.y, qt[e]);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars->tailfree[s]);
+  };
+  bool full = nbr > 0;
+  pump();
+  for (int j = 0; full && j < nbr; ++j) {
+    // H~^T of batch j in its slot: its tail terms (tail slot j & 1 last held
+    // batch j - 2, read out before chi of j - 2 came in)
+    full = wait_pump(&bars->fafull[j & 1], (uint32_t)(j >> 1) & 1u);
+    if (!full) break;
+    tail_ab(j);
+    if (j >= 1) {
+      full = wait_pump(&bars->chiready[(j - 1) & 1], (uint32_t)((j - 1) >> 1) & 1u);
+      if (full) tail_chi(j - 1);
+    }
+  }
+  if (full) full = wait_pump(&bars->chiready[(nbr - 1) & 1], (uint32_t)((nbr - 1) >> 1) & 1u);
+  if (full) tail_chi(nbr - 1);
+  if (full && !*abort && lane < K) {                   // the tail rows of this cluster's slice
+    #pragma unroll
+    for (int e = 0; e < FU_TAIL_MAX; ++e)
+      if (e < tailE) {
+        rowPart[(int64_t)(row0 + e) * K + lane] = pt[e];
+        rowPart[F * K + (int64_t)(row0 + e) * K + lane] = qt[e];
+      }
+  }
+  return issued;
+}
+
 // One launch per iteration; grid = ncl clusters x c blocks. BATCH: the
 // clusters run work items of many problems (FuParams::items).
-template <int BK, bool BATCH>
+template <int BK, bool BATCH, bool TAIL>
 __global__ void __launch_bounds__(FU_THREADS, 1)
 tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant__ CUtensorMap tmW0,
                 const __grid_constant__ CUtensorMap tmH0, Prob<float> P0, BetaParams bp, FuParams S) {
@@ -246,7 +466,14 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
   const int nb = b1 - b0;
   const int nv = S.nv;
   const FuLayout L = fu_layout(S.layK, S.laykp, nv);
+  // tail rows: their W~ rows, and per batch slot their A and B over the batch's columns
+  float* s_wtail = reinterpret_cast<float*>(base + L.tail);           // [FU_TAIL_MAX][32]
+  const float* s_tab = s_wtail + FU_TAIL_MAX * 32;                    // [2][FU_TAIL_MAX][2][128]
   const int64_t m0 = (int64_t)r * 128;
+  // TAIL (one problem, S.tail > 0): the last block's warp 0 takes rows
+  // 128 c .. 128 c + tailE - 1, and warp 3 joins the exchange
+  const int tailE = (TAIL && r == c - 1) ? S.tail : 0;
+  constexpr int nex = TAIL ? 5 : 4;                         // exchange warps
   const uint64_t lim = S.limitNs;
   const int ntiles = 4 * nb;
   const int vPre = nv < ntiles ? nv : ntiles;
@@ -259,7 +486,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
     prefetch_tmap(tmV);
     prefetch_tmap(tmW);
     prefetch_tmap(tmH);
-    fu_init_bars(bars, nv, c, S.extra);
+    fu_init_bars(bars, nv, c, nex, S.extra);
   }
   fence_before_sync();
   __syncthreads();
@@ -293,6 +520,10 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
   }
   for (uint32_t o = tid * 16u; o < 2u * L.chiSlot; o += FU_THREADS * 16u)
     *reinterpret_cast<uint4*>(base + L.chi0 + o) = make_uint4(0u, 0u, 0u, 0u);
+  if (TAIL && tid < FU_TAIL_MAX * 32) {
+    const int e = tid >> 5, k = tid & 31;
+    s_wtail[tid] = (e < tailE && k < K) ? P.W[(int64_t)(128 * c + e) * K + k] : 0.f;
+  }
   fence_smem_to_async();
   // every block of the cluster has its barriers and buffers ready before any
   // block arrives on them or writes into them; block 0 of the cluster decides
@@ -323,16 +554,46 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       for (int j = 0; j < faPre; ++j) mbar_wait(&bars.fafull[j], 0u, 100000000ull);
     }
     int issued = faPre < nbr ? faPre : nbr;
-    for (int j = issued; j < nbr; ++j, ++issued) {
+    auto issue = [&](int j) {
       const int s = j & 1;
-      if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.fafree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
-                                                       S.status, lim)))
-        break;
       if (elect_one()) {
         mbar_arrive_expect_tx(&bars.fafull[s], FU_TB);
         tma_load_2d(base + L.fa0 + s * FU_TB, tmH, 0, (int)(128 * (int64_t)(b0 + j)), &bars.fafull[s]);
       }
       __syncwarp();
+    };
+    if (!TAIL || tailE == 0) {
+      for (int j = issued; j < nbr; ++j, ++issued) {
+        if (j >= 2 && !__all_sync(0xffffffffu, fu_wait(&bars.fafree[j & 1], (uint32_t)((j - 2) >> 1) & 1u, &s_abort,
+                                                         S.status, lim)))
+          break;
+        issue(j);
+      }
+    } else {
+      FuTail A;
+      A.V = P.V;
+      A.ldv = P.ldv;
+      A.N = P.N;
+      A.F = P.F;
+      A.rowPart = P.rowPart + (int64_t)slice * 2 * P.F * K;
+      A.K = K;
+      A.kp = kp;
+      A.row0 = 128 * c;
+      A.tailE = tailE;
+      A.b0 = b0;
+      A.nbr = nbr;
+      A.issued = issued;
+      A.fa = base + L.fa0;
+      A.chi = base + L.chi0;
+      A.chiSlot = L.chiSlot;
+      A.tmH = tmH;
+      A.bars = &bars;
+      A.wtail = s_wtail;
+      A.tab = s_wtail + FU_TAIL_MAX * 32;
+      A.abort = &s_abort;
+      A.status = S.status;
+      A.lim = lim;
+      issued = fu_tail_warp<BK>(A, bp, lossHi, lossLo);
     }
     // after a timeout no copy may land once the block has ended: wait (bounded)
     // for the last loads of each slot (their consumers may have given up)
@@ -524,16 +785,19 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.stashfull);
     }
-  } else if (warp >= FU_EX0) {
+  } else if (warp >= FU_EX0 || (TAIL && warp == 3)) {
     // ---------------- cluster exchange ----------------
-    // Thread x (0..127) owns TMEM lane x = column x of the batch for the
-    // mailbox write. The batch's K x 32 tasks (row k, four columns 4u .. 4u
-    // + 3; task t = 32 k + u) are split evenly over the cluster's blocks:
-    // block r reduces tasks [32 K r / c, 32 K (r + 1) / c).
-    // Each warp publishes what it wrote itself (warp barrier, one fence at
-    // cluster scope, relaxed arrivals; the cluster barriers count 4 c
-    // arrivals), so the four warps never wait for one another.
-    const int x = tid - FU_EX0 * 32;
+    // Thread x < 128 (the first four warps) owns TMEM lane x = column x of
+    // the batch for the mailbox write. The batch's K x 32 tasks (row k, four
+    // columns 4u .. 4u + 3; task t = 32 k + u) are split evenly over the
+    // cluster's blocks: block r reduces tasks [32 K r / c, 32 K (r + 1) / c),
+    // over all five warps (one task per thread up to 160 a block). Each warp
+    // publishes what it wrote itself (warp barrier, one fence at cluster
+    // scope, relaxed arrivals; the mailbox barriers count the 4 c reading
+    // warps, the chi barriers the 5 c warps), so the warps never wait for one
+    // another.
+    const int x = (TAIL && warp == 3) ? 128 + lane : tid - FU_EX0 * 32;   // 0 .. 32 nex - 1
+    const bool rd = !TAIL || warp != 3;               // reads TMEM lanes 32 (warp & 3) .. + 31 into the mailbox
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int tLo = 32 * K * r / c, ntask = 32 * K * (r + 1) / c - tLo;
     const uint32_t mbS = smem_u32(base + L.mb);
@@ -547,8 +811,13 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       // handshake of batch j completes: each block writes its mailbox after
       // its H contraction of batch j, whose completion covers its W
       // contraction of batch j - 2. So two handshakes per batch suffice.
-      bool go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull, (uint32_t)j & 1u, &s_abort, S.status, lim));
-      if (go) {
+      bool go = true;
+      if (rd) {
+        go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull, (uint32_t)j & 1u, &s_abort, S.status, lim));
+        if (TAIL && go && tailE > 0)                  // the tail rows' A, B of this batch
+          go = __all_sync(0xffffffffu, fu_wait(&bars.tailfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim));
+      }
+      if (rd && go) {
         fence_after_sync();
         for (int k0 = 0; k0 < kp; k0 += 16) {
           float hn[16], hd[16];
@@ -562,13 +831,36 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
               mb[(K + k0 + i) * 128 + x] = hd[i];
             }
         }
+        if (TAIL && tailE > 0) {                      // plus the tail rows' terms W~[f, k] A[f, n], W~[f, k] B[f, n]
+          float ta[FU_TAIL_MAX], tb[FU_TAIL_MAX];
+          #pragma unroll
+          for (int e = 0; e < FU_TAIL_MAX; ++e) {
+            ta[e] = s_tab[((s * FU_TAIL_MAX + e) * 2 + 0) * 128 + x];   // (zero past tailE, like s_wtail)
+            tb[e] = s_tab[((s * FU_TAIL_MAX + e) * 2 + 1) * 128 + x];
+          }
+          for (int k = 0; k < K; ++k) {
+            float vn = mb[k * 128 + x], vd = mb[(K + k) * 128 + x];
+            #pragma unroll
+            for (int e = 0; e < FU_TAIL_MAX; ++e) {
+              vn = fmaf(s_wtail[32 * e + k], ta[e], vn);
+              vd = fmaf(s_wtail[32 * e + k], tb[e], vd);
+            }
+            mb[k * 128 + x] = vn;
+            mb[(K + k) * 128 + x] = vd;
+          }
+        }
         fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars.haccfree);
+        // chi slot s is rewritten once every block's mailbox of this batch is
+        // out: warp 0 must have read chi of batch j - 2 from it first
+        if (TAIL && tailE > 0 && j >= 2)
+          go = __all_sync(0xffffffffu, fu_wait(&bars.tailfree[s], (uint32_t)((j - 2) >> 1) & 1u, &s_abort, S.status,
+                                               lim));
         // each warp publishes its own columns: warp barrier (cumulative), one
         // fence at cluster scope, relaxed arrivals
         __syncwarp();
-        if (lane == 0 && !s_abort) {
+        if (go && lane == 0 && !s_abort) {
           fence_acq_rel_cluster();
           for (int q = 0; q < c; ++q) mbar_arrive_remote_relaxed(dsmem_map(&bars.mailfull[s], (uint32_t)q));
         }
@@ -590,7 +882,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
                                                                S.status, lim));
       // tasks of (row k, 4 columns): the four columns' numerators and
       // denominators of up to four ranks in flight together, summed in rank order
-      for (int task = x; go && task < ntask; task += 128) {
+      for (int task = x; go && task < ntask; task += 32 * nex) {
         const int k = (tLo + task) >> 5, n4 = 4 * ((tLo + task) & 31);
         const uint32_t on = mbS + (uint32_t)(k * 512 + 4 * n4), od = mbS + (uint32_t)((K + k) * 512 + 4 * n4);
         float ht[4];
@@ -1080,16 +1372,39 @@ cudaError_t launch_fused_batch_copies(const Plan<float>& pl, const int* prefHc, 
   return cudaGetLastError();
 }
 
+// Blocks per cluster and tail rows of one problem: F = 128 c + tail with
+// 1 <= tail <= FU_TAIL_MAX takes c = F / 128 blocks (warp 0 of the last one
+// has the tail rows), else c = ceil(F / 128) and no tail (NMF_FU_TAIL=0: never
+// a tail).
+static void fu_geometry(int64_t F, int* c, int* tail) {
+  const char* env = std::getenv("NMF_FU_TAIL");
+  const bool allow = !(env && std::atoi(env) == 0);
+  const int t = (int)(F % 128);
+  if (allow && F > 128 && t >= 1 && t <= FU_TAIL_MAX) {
+    *c = (int)(F / 128);
+    *tail = t;
+  } else {
+    *c = (int)((F + 127) / 128);
+    *tail = 0;
+  }
+}
+
+int tc_fused_cluster_blocks(const Prob<float>& P) {
+  int c = 0, t = 0;
+  fu_geometry(P.F, &c, &t);
+  return c;
+}
+
 bool tc_fused_supported(const Prob<float>& P) {
   return P.sWS && P.kp <= 32 && P.F <= 1024 && fu_pick_nv(P.K, P.kp) >= 2;
 }
 
 int tc_fused_clusters(const Prob<float>& P, int sms) {
-  const int c = (int)((P.F + 127) / 128);
+  const int c = tc_fused_cluster_blocks(P);
   const int nbatch = (int)((P.N + 127) / 128);
   const int nv = fu_pick_nv(P.K, P.kp);
   const size_t sm = 1024 + fu_layout(P.K, P.kp, nv).total;
-  auto kern = tc_fused_kernel<BK_GENERAL, false>;
+  auto kern = tc_fused_kernel<BK_GENERAL, false, false>;
   if (ensure_smem_attr(reinterpret_cast<const void*>(kern), sm) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1122,7 +1437,7 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   FuParams S;
   memset(&S, 0, sizeof(S));
   S.gH = gH;
-  S.c = (int)((P.F + 127) / 128);
+  fu_geometry(P.F, &S.c, &S.tail);
   S.nbatch = (int)((P.N + 127) / 128);
   S.ncl = ncl;
   S.nv = fu_pick_nv(P.K, P.kp);
@@ -1161,8 +1476,13 @@ cudaError_t launch_tc_fused(const Prob<float>& P, const TcMaps& m, const BetaPar
   cudaError_t e = cudaSuccess;
 #define NMF_FU_CASE(BKV)                                                                   \
   case BKV:                                                                                \
-    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, false>), sm);  \
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, false>, tmV, m.wsA, m.htB, P, bp, S); \
+    if (S.tail > 0) {                                                                      \
+      e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, false, true>), sm);  \
+      if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, false, true>, tmV, m.wsA, m.htB, P, bp, S); \
+    } else {                                                                               \
+      e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, false, false>), sm);  \
+      if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, false, false>, tmV, m.wsA, m.htB, P, bp, S); \
+    }                                                                                      \
     break;
   switch (bp.kind) {
     NMF_FU_CASE(BK_IS)
@@ -1219,8 +1539,8 @@ cudaError_t launch_tc_fused_batch(const FuBatch& fb, const BetaParams& bp, int* 
   cudaError_t e = cudaSuccess;
 #define NMF_FU_CASE(BKV)                                                                  \
   case BKV:                                                                               \
-    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, true>), sm);  \
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, true>, none, none, none, P0, bp, S); \
+    e = ensure_smem_attr(reinterpret_cast<const void*>(tc_fused_kernel<BKV, true, false>), sm);  \
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<BKV, true, false>, none, none, none, P0, bp, S); \
     break;
   switch (bp.kind) {
     NMF_FU_CASE(BK_IS)

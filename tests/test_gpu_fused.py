@@ -54,10 +54,13 @@ def rel(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
 
 
-@pytest.mark.parametrize("shape", [(100, 300, 4), (200, 333, 20), (361, 517, 32), (513, 1000, 20)])
+@pytest.mark.parametrize("shape", [(100, 300, 4), (200, 333, 20), (361, 517, 32), (513, 1000, 20), (129, 260, 8),
+                                   (258, 700, 32)])
 @pytest.mark.parametrize("beta", [0.0, 1.0, 1.5, 2.0])
 def test_one_iteration_matches_oracle(lib, shape, beta):
-    """Clusters of 1, 2, 3 and 5 blocks; ragged rows (F % 128) and columns (N % 128)."""
+    """Clusters of 1, 2, 3 and 4 blocks; ragged rows (F % 128) and columns (N %
+    128); F = 513, 129 and 258 put their last 1 or 2 rows on the last block's
+    tail-row warp (clusters of 4, 1 and 2 blocks)."""
     F, N, K = shape
     V, W0, H0 = problem(F, N, K, seed=F + N)
     W, H, loss = run_bf16(V, W0, H0, beta)
@@ -93,6 +96,28 @@ def test_w_half_launch_shapes(lib, shape, beta):
         del os.environ["NMF_FU_POST"]
     assert rel(W1, W2) < 1e-5 and rel(H1, H2) < 1e-5
     assert loss1 == loss2
+
+
+@pytest.mark.parametrize("shape,beta", [((513, 2000, 20), 0.0), ((258, 900, 12), 1.5)])
+def test_tail_rows_against_full_blocks(lib, shape, beta):
+    """The tail rows (F = 128 c + 1 or 2 on the last block's warp 0, in FP32)
+    and the plain layout (NMF_FU_TAIL=0: one more block per cluster) both
+    match the oracle over three iterations, and each other to the bf16
+    tolerance."""
+    import os
+    F, N, K = shape
+    V, W0, H0 = problem(F, N, K, seed=F + 11)
+    W, H, loss = run_bf16(V, W0, H0, beta, iters=3)
+    os.environ["NMF_FU_TAIL"] = "0"
+    try:
+        W2, H2, loss2 = run_bf16(V, W0, H0, beta, iters=3)
+    finally:
+        del os.environ["NMF_FU_TAIL"]
+    Wo, Ho, lo = oracle_h_first(V, W0, H0, beta, iters=3)
+    for Wx, Hx, lx in ((W, H, loss), (W2, H2, loss2)):
+        assert rel(Wx, Wo) < 3 * TOL_WH and rel(Hx, Ho) < 3 * TOL_WH
+        assert lx == pytest.approx(lo[2], rel=TOL_D)
+    assert rel(W, W2) < 3 * TOL_WH and rel(H, H2) < 3 * TOL_WH
 
 
 @pytest.mark.parametrize("beta", [-1.0, 0.5, 3.0])
