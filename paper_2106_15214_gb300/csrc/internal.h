@@ -326,7 +326,7 @@ cudaError_t launch_tc_ws_col(const Prob<float>& P, const TcMaps& m, int csel, in
 // normalisation), one [P | Q] partial slice per cluster into rowPart (ncl
 // slices) and one objective partial per block (grid = ceil(F / 128) x ncl).
 // Blocks per cluster of the single-problem fused sweep (ceil(F / 128), or
-// F / 128 when the last block also takes 1 or 2 tail rows).
+// F / 128 when the last block also takes the tail row of F = 128 c + 1).
 int tc_fused_cluster_blocks(const Prob<float>& P);
 bool tc_fused_supported(const Prob<float>& P);
 // Clusters of ceil(F / 128) blocks that can be resident at once (at most the

@@ -9,10 +9,10 @@
 //
 // Work split. A cluster of c blocks owns a run of 128-column batches of V;
 // block r of the cluster owns rows [128 r, 128 r + 128) (the TMEM lanes of its
-// tiles). c = ceil(F / 128), except when F = 128 c + t with 1 <= t <= 2 (a
-// spectrogram's F = 2^m + 1 frequency bins): then the last block's warp 0 also
-// takes the t rows past its 128 in FP32, so that one block per cluster less
-// is needed (more clusters fit on the GPU). Per batch each block
+// tiles). c = ceil(F / 128), except when F = 128 c + 1 (a spectrogram's
+// F = 2^m + 1 frequency bins): then the last block's warp 0 also takes the row
+// past its 128 in FP32, so that one block per cluster less is needed (36
+// clusters of 4 instead of 28 of 5 at F = 513). Per batch each block
 //   1. forms Vt (128 x 128, tcgen05 kind::tf32, W~ rows in TMEM, H~^T rows in
 //      shared memory) and, tile by tile (32 columns), reads V, evaluates A, B
 //      and the objective in registers (FP32; FP64 below the small-Vt guard),
@@ -69,7 +69,7 @@ constexpr int FU_EX0 = 20;           // first exchange warp
 // exchange warps: 20-23 read the H accumulator (one TMEM lane quarter each)
 // and reduce; with tail rows (clusters of F / 128 blocks, 25 % more tasks a
 // block) warp 3 reduces too
-constexpr int FU_TAIL_MAX = 2;       // rows past the last block's 128 handled in FP32 by warp 0 (F = 128 c + tail)
+constexpr int FU_TAIL_MAX = 1;       // rows past the last block's 128 handled in FP32 by warp 0 (F = 128 c + tail)
 constexpr size_t FU_STATIC_RESERVE = 1024;   // the kernel's static shared memory (barriers)
 // tail-row buffers: W~ rows [FU_TAIL_MAX][32], then A, B per slot [2][FU_TAIL_MAX][2][128] (floats)
 constexpr uint32_t FU_TAIL_BYTES = 4u * (FU_TAIL_MAX * 32 + 2 * FU_TAIL_MAX * 2 * 128);
@@ -229,13 +229,13 @@ __device__ __forceinline__ void fu_init_bars(FuBars& B, int nv, int c, int nex, 
   fence_mbar_init();
 }
 
-// ---- tail rows (F = 128 c + t, t <= FU_TAIL_MAX): warp 0 of the last block --
+// ---- tail rows (F = 128 c + t, t <= FU_TAIL_MAX = 1): warp 0 of the last block --
 //
 // The rows past the block's 128 TMEM lanes, in FP32 between the warp's H~^T
 // loads. Per batch j, once its H~^T rows are in their slot: the rows' product
 // with H~ (the TF32 values MMA1 reads), A, B and objective terms, four
-// columns per lane, into tail slot j & 1 for the exchange warps, which add the
-// rows' terms to the block's H partials. Once chi of batch j is in: the rows'
+// columns per lane, into tail slot j & 1, from which the cluster's owners add
+// the rows' terms to the H numerator and denominator of their tasks. Once chi of batch j is in: the rows'
 // W numerators and denominators, lane k summing over the batch's columns in
 // order, accumulated over the batches and written into the cluster's slice at
 // the end. A load goes out as soon as its slot is free (MMA1 and these
@@ -520,9 +520,9 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
   }
   for (uint32_t o = tid * 16u; o < 2u * L.chiSlot; o += FU_THREADS * 16u)
     *reinterpret_cast<uint4*>(base + L.chi0 + o) = make_uint4(0u, 0u, 0u, 0u);
-  if (TAIL && tid < FU_TAIL_MAX * 32) {
+  if (TAIL && tid < FU_TAIL_MAX * 32) {              // (every block: the owners add the tail rows' terms)
     const int e = tid >> 5, k = tid & 31;
-    s_wtail[tid] = (e < tailE && k < K) ? P.W[(int64_t)(128 * c + e) * K + k] : 0.f;
+    s_wtail[tid] = (e < S.tail && k < K) ? P.W[(int64_t)(128 * c + e) * K + k] : 0.f;
   }
   fence_smem_to_async();
   // every block of the cluster has its barriers and buffers ready before any
@@ -814,7 +814,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
       bool go = true;
       if (rd) {
         go = __all_sync(0xffffffffu, fu_wait(&bars.haccfull, (uint32_t)j & 1u, &s_abort, S.status, lim));
-        if (TAIL && go && tailE > 0)                  // the tail rows' A, B of this batch
+        if (TAIL && go && tailE > 0)                  // the tail rows' A, B of this batch, read by the owners
           go = __all_sync(0xffffffffu, fu_wait(&bars.tailfull[s], (uint32_t)(j >> 1) & 1u, &s_abort, S.status, lim));
       }
       if (rd && go) {
@@ -830,24 +830,6 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
               mb[(k0 + i) * 128 + x] = hn[i];
               mb[(K + k0 + i) * 128 + x] = hd[i];
             }
-        }
-        if (TAIL && tailE > 0) {                      // plus the tail rows' terms W~[f, k] A[f, n], W~[f, k] B[f, n]
-          float ta[FU_TAIL_MAX], tb[FU_TAIL_MAX];
-          #pragma unroll
-          for (int e = 0; e < FU_TAIL_MAX; ++e) {
-            ta[e] = s_tab[((s * FU_TAIL_MAX + e) * 2 + 0) * 128 + x];   // (zero past tailE, like s_wtail)
-            tb[e] = s_tab[((s * FU_TAIL_MAX + e) * 2 + 1) * 128 + x];
-          }
-          for (int k = 0; k < K; ++k) {
-            float vn = mb[k * 128 + x], vd = mb[(K + k) * 128 + x];
-            #pragma unroll
-            for (int e = 0; e < FU_TAIL_MAX; ++e) {
-              vn = fmaf(s_wtail[32 * e + k], ta[e], vn);
-              vd = fmaf(s_wtail[32 * e + k], tb[e], vd);
-            }
-            mb[k * 128 + x] = vn;
-            mb[(K + k) * 128 + x] = vd;
-          }
         }
         fence_before_sync();
         __syncwarp();
@@ -892,6 +874,12 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
           ht[i] = task == x ? htp[i] : (n < P.N ? __ldg(&P.Ht[(int64_t)k * P.N + n]) : 1.f);
         }
         float hn[4] = {0.f, 0.f, 0.f, 0.f}, hd[4] = {0.f, 0.f, 0.f, 0.f};
+        float4 tA = make_float4(0.f, 0.f, 0.f, 0.f), tB = tA;
+        if (TAIL) {                                   // the tail rows' A, B at these columns (last block's slot s)
+          const uint32_t ta = smem_u32(s_tab + (s * FU_TAIL_MAX * 2 + 0) * 128 + n4);
+          tA = dsmem_ld4(dsmem_map_addr(ta, (uint32_t)(c - 1)));
+          tB = dsmem_ld4(dsmem_map_addr(ta + 512u, (uint32_t)(c - 1)));
+        }
         for (int q0 = 0; q0 < c; q0 += 4) {
           float4 pn[4], pd[4];
           #pragma unroll
@@ -906,6 +894,11 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmV0, const __grid_constant_
               hn[0] += pn[u].x; hn[1] += pn[u].y; hn[2] += pn[u].z; hn[3] += pn[u].w;
               hd[0] += pd[u].x; hd[1] += pd[u].y; hd[2] += pd[u].z; hd[3] += pd[u].w;
             }
+        }
+        if (TAIL) {                                   // + W~[f, k] A[f, n], W~[f, k] B[f, n] of the tail row
+          const float w = s_wtail[k];
+          hn[0] = fmaf(w, tA.x, hn[0]); hn[1] = fmaf(w, tA.y, hn[1]); hn[2] = fmaf(w, tA.z, hn[2]); hn[3] = fmaf(w, tA.w, hn[3]);
+          hd[0] = fmaf(w, tB.x, hd[0]); hd[1] = fmaf(w, tB.y, hd[1]); hd[2] = fmaf(w, tB.z, hd[2]); hd[3] = fmaf(w, tB.w, hd[3]);
         }
         float c1[4], c2[4];
         #pragma unroll
@@ -1373,9 +1366,9 @@ cudaError_t launch_fused_batch_copies(const Plan<float>& pl, const int* prefHc, 
 }
 
 // Blocks per cluster and tail rows of one problem: F = 128 c + tail with
-// 1 <= tail <= FU_TAIL_MAX takes c = F / 128 blocks (warp 0 of the last one
-// has the tail rows), else c = ceil(F / 128) and no tail (NMF_FU_TAIL=0: never
-// a tail).
+// 1 <= tail <= FU_TAIL_MAX (= 1) takes c = F / 128 blocks (warp 0 of the last
+// one has the tail row), else c = ceil(F / 128) and no tail (NMF_FU_TAIL=0:
+// never a tail).
 static void fu_geometry(int64_t F, int* c, int* tail) {
   const char* env = std::getenv("NMF_FU_TAIL");
   const bool allow = !(env && std::atoi(env) == 0);
