@@ -216,15 +216,17 @@ def test_unsupported_forms_are_rejected(lib):
     m.close()
 
 
-def test_cluster_wait_timeout_returns_etimeout(lib):
+@pytest.mark.parametrize("F", [200, 257])
+def test_cluster_wait_timeout_returns_etimeout(lib, F):
     """The cluster exchange's waits expect one arrival more than there are
     blocks (nmf_set_barrier_test): every such wait runs out after 2 ms, the
     step returns NMF_ETIMEOUT with W and H restored, and the context then
-    computes the oracle's iterate with the defaults back."""
+    computes the oracle's iterate with the defaults back. F = 257: the tail
+    row's warp (which polls its loads while it waits) gives up too."""
     import torch
     from paper_2106_15214_gb300.binding import NMF, NMF_ETIMEOUT, NMFError, check
-    V, W0, H0 = problem(200, 333, 20, seed=3)
-    m = NMF(200, 333, 20, 1.0, precision="bf16", order="H")
+    V, W0, H0 = problem(F, 333, 20, seed=3)
+    m = NMF(F, 333, 20, 1.0, precision="bf16", order="H")
     Vd = torch.tensor(V, dtype=torch.float32, device="cuda")
     W = torch.tensor(W0, dtype=torch.float32, device="cuda")
     H = torch.tensor(H0, dtype=torch.float32, device="cuda")
@@ -245,16 +247,18 @@ def test_cluster_wait_timeout_returns_etimeout(lib):
     m.close()
 
 
+@pytest.mark.parametrize("F", [300, 257])
 @pytest.mark.parametrize("beta", [0.0, 1.0])
-def test_kappa_and_no_normalisation(lib, beta):
+def test_kappa_and_no_normalisation(lib, beta, F):
     """kappa > 0 (Sec. 4.1.3: added to V and to every product) and the step
     without the normalisation (the last kernel then only makes the next
-    iteration's copies), three iterations in one call."""
+    iteration's copies), three iterations in one call; F = 257 with the tail
+    row on the last block's warp 0."""
     import torch
     from paper_2106_15214_gb300.binding import NMF
-    V, W0, H0 = problem(300, 700, 20, seed=21)
+    V, W0, H0 = problem(F, 700, 20, seed=21)
     for kappa, normalize in ((0.05, True), (0.0, False), (0.05, False)):
-        m = NMF(300, 700, 20, beta, precision="bf16", order="H", kappa=kappa, normalize=normalize)
+        m = NMF(F, 700, 20, beta, precision="bf16", order="H", kappa=kappa, normalize=normalize)
         W = torch.tensor(W0, dtype=torch.float32, device="cuda")
         H = torch.tensor(H0, dtype=torch.float32, device="cuda")
         m.set_dense(torch.tensor(V, dtype=torch.float32, device="cuda"))
