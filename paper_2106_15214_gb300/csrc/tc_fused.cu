@@ -29,7 +29,7 @@
 //   4. contracts its TMEM copy of A and B with chi_1, chi_2 (kind::f16) into
 //      its W numerator and denominator (TMEM, accumulated over the batches).
 // At the end every block writes its [P | Q] rows as one partial slice (one per
-// cluster); the W epilogue kernel sums the slices in fixed order. The next
+// cluster); fused_w_kernel sums the slices in fixed order. The next
 // batch's product and epilogue overlap the exchange: three TMEM batch buffers,
 // two H~^T slots and two chi slots alternate.
 //
